@@ -1,0 +1,200 @@
+/*
+ * mickey.h -- C ABI of the bitsliced MICKEY 2.0 keystream library for GB300
+ * (sm_103a).
+ *
+ * The library generates MICKEY 2.0 keystreams for many independent
+ * (key, IV) instances at once.  Internally it uses the column-major
+ * "bitsliced" representation of Sec. IV-A: a 32-bit word holds the same
+ * register bit of 32 instances, so one GPU thread clocks 32 ciphers
+ * (Sec. IV-D: 200 words for the 100-bit R and S registers).  Instances
+ * 32g .. 32g+31 form group g.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  keys      n x 10 bytes, instance-major.  Key bit k_i is bit (7 - i%8) of
+ *            byte i/8 (MSB first).
+ *  ivs       n x 10 bytes.  Only the first iv_lens[i] bits of row i are
+ *            used, same bit order.
+ *  iv_lens   n values in [0, 80]; NULL means 80 for every instance.
+ *  keystream bit z_t of an instance is the t-th output bit after the
+ *            key/IV loading and the 100 preclocks of the cipher.
+ *  Errors    functions returning int give MICKEY_OK (0) or a negative
+ *            MICKEY_E_* code; functions returning a pointer give NULL.  In
+ *            both cases mickey_last_error() and mickey_last_error_message()
+ *            report the cause (thread-local).  Errors raised inside a kernel
+ *            surface at the next mickey_sync() on that handle.
+ *  Streams   device work is enqueued on the CUDA stream given at creation
+ *            or by mickey_set_stream() (a cudaStream_t passed as void*;
+ *            NULL is the legacy default stream).  Calls return once the
+ *            work is enqueued unless stated otherwise.
+ *  Threads   a handle must not be used by two host threads at once.
+ *
+ * Output layouts (argument `layout`), for a call producing n_bits per
+ * instance:
+ *  MICKEY_LAYOUT_BITSLICED_U32 (0)  uint32 [G][n_bits], G = ceil(n/32):
+ *        word [g][t] has bit l = z_t of instance 32g+l (Sec. IV-A layout);
+ *        bits of lanes past instance n-1 are zero.  Size 4*G*n_bits bytes.
+ *  MICKEY_LAYOUT_BYTES (1)  uint8 [n][ceil(n_bits/8)], row-major: byte j of
+ *        row i holds z_{8j..8j+7} of instance i, z_{8j} in bit 7; unused low
+ *        bits of a last partial byte are zero.
+ *  MICKEY_LAYOUT_U32 (2)  uint32 [n][n_bits/32]: word k of row i holds
+ *        z_{32k..32k+31}, z_{32k} in bit 31.  Needs n_bits % 32 == 0.
+ *  MICKEY_LAYOUT_U32_F32 (3)  the U32 array followed by float32
+ *        [n][n_bits/32] with f = (w >> 8) * 2^-24 for the same word w: an
+ *        exact uniform on [0, 1 - 2^-24].  Needs n_bits % 32 == 0.
+ */
+#ifndef MICKEY_H
+#define MICKEY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MICKEY_API __attribute__((visibility("default")))
+#else
+#define MICKEY_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MICKEY_OK 0
+#define MICKEY_E_ARG (-1)     /* NULL pointer, zero/oversized count, bad flag */
+#define MICKEY_E_IVLEN (-2)   /* an IV length above 80 bits */
+#define MICKEY_E_LIMIT (-3)   /* more than 2^40 keystream bits per key/IV */
+#define MICKEY_E_LAYOUT (-4)  /* unknown layout or n_bits it cannot hold */
+#define MICKEY_E_OOM (-5)     /* device or host allocation failed */
+#define MICKEY_E_CUDA (-6)    /* a CUDA runtime call failed */
+#define MICKEY_E_TIMEOUT (-7) /* a bounded device-side wait ran out */
+#define MICKEY_E_STATE (-8)   /* handle not usable for this call */
+
+#define MICKEY_LAYOUT_BITSLICED_U32 0
+#define MICKEY_LAYOUT_BYTES 1
+#define MICKEY_LAYOUT_U32 2
+#define MICKEY_LAYOUT_U32_F32 3
+
+#define MICKEY_MEM_HOST 0   /* pointer arguments are host memory */
+#define MICKEY_MEM_DEVICE 1 /* pointer arguments are device memory */
+
+#define MICKEY_KEY_BYTES 10
+#define MICKEY_MAX_IV_BITS 80
+/* Sec. II-C-1: up to 2^40 keystream bits may be produced per key/IV pair. */
+#define MICKEY_MAX_STREAM_BITS (1ull << 40)
+
+typedef struct mickey_streams mickey_streams;
+
+/* --------------------------------------------------------------------------
+ * Creation: key/IV loading and preclocking (Sec. IV-D; the cipher's
+ * initialisation of the specification the paper cites): R = S = 0, one
+ * mixing clock per IV bit, one per key bit, then 100 mixing clocks with
+ * input 0 -- for all n instances, bitsliced, on the device.
+ * ------------------------------------------------------------------------ */
+
+/* Host inputs, legacy default stream.  The library copies keys, ivs and
+ * iv_lens; the caller keeps ownership.  Errors: MICKEY_E_ARG (keys or ivs
+ * NULL, n == 0), MICKEY_E_IVLEN, MICKEY_E_OOM, MICKEY_E_CUDA. */
+MICKEY_API mickey_streams *mickey_init_streams(const uint8_t *keys, const uint8_t *ivs,
+                                    const uint32_t *iv_lens, size_t n);
+
+/* As mickey_init_streams, with the inputs' memory space `mem`
+ * (MICKEY_MEM_HOST or MICKEY_MEM_DEVICE) and the CUDA stream the handle
+ * uses from now on.  Device inputs must stay valid until the work is done
+ * (mickey_sync); an IV length above 80 in device memory is reported as
+ * MICKEY_E_IVLEN by mickey_sync. */
+MICKEY_API mickey_streams *mickey_init_streams_ex(const void *keys, const void *ivs,
+                                       const uint32_t *iv_lens, size_t n,
+                                       int mem, void *cuda_stream);
+
+/* Re-key an existing handle in place (same n, no allocation): runs the
+ * whole loading and preclocking again and resets every position to 0. */
+MICKEY_API int mickey_reset_streams(mickey_streams *s, const void *keys, const void *ivs,
+                         const uint32_t *iv_lens, int mem);
+
+/* Use `cuda_stream` for this handle's later work. */
+MICKEY_API int mickey_set_stream(mickey_streams *s, void *cuda_stream);
+
+/* --------------------------------------------------------------------------
+ * Keystream: for t in 0..n_bits-1, z_t = r0 ^ s0, then one non-mixing
+ * CLOCK_KG with input 0, for every instance (Sec. IV-D: 32 keystream bits per
+ * thread per clock).  Stateful: each call continues every stream where the
+ * previous call stopped.  `out` is a caller-owned DEVICE buffer of
+ * mickey_output_bytes(n, n_bits, layout) bytes.
+ * Errors: MICKEY_E_ARG (s or out NULL, n_bits == 0), MICKEY_E_LAYOUT,
+ * MICKEY_E_LIMIT (a stream would pass 2^40 bits), MICKEY_E_CUDA.
+ * ------------------------------------------------------------------------ */
+MICKEY_API int mickey_generate(mickey_streams *s, uint64_t n_bits, void *out, int layout);
+
+/* Bytes one call writes for n instances and n_bits per instance; 0 when the
+ * layout cannot hold n_bits. */
+MICKEY_API size_t mickey_output_bytes(size_t n, uint64_t n_bits, int layout);
+
+/* As mickey_generate into a HOST buffer (pinned memory gives full copy
+ * speed).  Generation runs in chunks on the device and each chunk is copied
+ * back while the next one is generated.  Returns after the data is in
+ * `host_out`.  Extra errors: MICKEY_E_OOM for the staging buffers. */
+MICKEY_API int mickey_generate_host(mickey_streams *s, uint64_t n_bits, void *host_out,
+                         int layout);
+
+/* Wait for the handle's stream; report a device-side error if one was
+ * raised (MICKEY_E_IVLEN, MICKEY_E_TIMEOUT) or a CUDA error. */
+MICKEY_API int mickey_sync(mickey_streams *s);
+
+MICKEY_API size_t mickey_num_streams(const mickey_streams *s);
+/* Keystream bits generated so far by instance i (UINT64_MAX if i >= n). */
+MICKEY_API uint64_t mickey_position(const mickey_streams *s, size_t i);
+
+/* --------------------------------------------------------------------------
+ * Checkpoint / resume.  A stream's state is 26 bytes: r0..r99 in bytes
+ * 0..12 then s0..s99 in bytes 13..25, bit i of a register at bit (7 - i%8)
+ * of byte i/8 of its half; unused low bits of bytes 12 and 25 are zero.
+ * ------------------------------------------------------------------------ */
+
+/* Copy every stream's state (n x 26 bytes) and position (n x uint64) to
+ * host buffers; synchronises the handle's stream.  positions may be NULL. */
+MICKEY_API int mickey_export_state(mickey_streams *s, uint8_t *states,
+                        uint64_t *positions);
+
+/* New handle from host states/positions written by mickey_export_state;
+ * positions may be NULL (all 0).  Errors as mickey_init_streams_ex. */
+MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
+                                    const uint64_t *positions, size_t n,
+                                    void *cuda_stream);
+
+/* Synchronise, release all device memory of the handle.  NULL is a no-op. */
+MICKEY_API void mickey_free(mickey_streams *s);
+
+/* --------------------------------------------------------------------------
+ * Errors and introspection
+ * ------------------------------------------------------------------------ */
+MICKEY_API int mickey_last_error(void);
+MICKEY_API const char *mickey_last_error_message(void);
+MICKEY_API const char *mickey_error_string(int code);
+
+/* The five constant tables compiled into the kernels, as 100-bit masks
+ * (bit i of table at word i/32, bit i%32): rows RTAPS, COMP0, COMP1, FB0,
+ * FB1.  Host-only, needs no GPU. */
+MICKEY_API void mickey_tables(uint32_t masks[5][4]);
+
+/* Algorithmic 32-bit logic operations of one bitsliced CLOCK_KG of one
+ * 32-lane group after constant folding into 3-input LOP3 (mixing = 0: a
+ * keystream clock including z = r0 ^ s0; mixing = 1: an init clock).
+ * Host-only. */
+MICKEY_API int mickey_ops_per_clock(int mixing);
+
+/* Measurement helper for the roofline: runs independent 3-input LOP3
+ * chains (blocks_per_sm * SM-count blocks of `threads` threads, `iters`
+ * x 128 LOP3 per thread) on the current device, synchronously.  Outputs
+ * (each may be NULL): LOP3 results per SM per SM-cycle, the SM clock seen
+ * (MHz), and the whole-GPU rate in 10^12 ops/s. */
+MICKEY_API int mickey_probe_lop3(int blocks_per_sm, int threads, int iters,
+                                 double *ops_per_sm_clk, double *sm_mhz, double *tops);
+
+/* Library version string. */
+MICKEY_API const char *mickey_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MICKEY_H */

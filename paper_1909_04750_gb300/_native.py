@@ -1,0 +1,96 @@
+"""ctypes binding of libmickey.so (the C ABI of include/mickey.h).
+
+Argument marshalling only: every step of the keystream path runs in the
+library's CUDA kernels.  If the library has not been built this module
+raises; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libmickey.so")
+
+OK = 0
+E_ARG, E_IVLEN, E_LIMIT, E_LAYOUT, E_OOM, E_CUDA, E_TIMEOUT, E_STATE = range(-1, -9, -1)
+LAYOUT_BITSLICED_U32, LAYOUT_BYTES, LAYOUT_U32, LAYOUT_U32_F32 = 0, 1, 2, 3
+MEM_HOST, MEM_DEVICE = 0, 1
+MAX_STREAM_BITS = 1 << 40
+
+_lock = threading.Lock()
+_lib = None
+
+c_void_p, c_size_t, c_uint64, c_int, c_char_p = (ctypes.c_void_p, ctypes.c_size_t,
+                                                 ctypes.c_uint64, ctypes.c_int,
+                                                 ctypes.c_char_p)
+
+# name: (restype, argtypes)
+SIGNATURES = {
+    "mickey_init_streams": (c_void_p, [c_void_p, c_void_p, c_void_p, c_size_t]),
+    "mickey_init_streams_ex": (c_void_p, [c_void_p, c_void_p, c_void_p, c_size_t, c_int,
+                                          c_void_p]),
+    "mickey_reset_streams": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "mickey_set_stream": (c_int, [c_void_p, c_void_p]),
+    "mickey_generate": (c_int, [c_void_p, c_uint64, c_void_p, c_int]),
+    "mickey_output_bytes": (c_size_t, [c_size_t, c_uint64, c_int]),
+    "mickey_generate_host": (c_int, [c_void_p, c_uint64, c_void_p, c_int]),
+    "mickey_sync": (c_int, [c_void_p]),
+    "mickey_num_streams": (c_size_t, [c_void_p]),
+    "mickey_position": (c_uint64, [c_void_p, c_size_t]),
+    "mickey_export_state": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "mickey_import_state": (c_void_p, [c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mickey_free": (None, [c_void_p]),
+    "mickey_last_error": (c_int, []),
+    "mickey_last_error_message": (c_char_p, []),
+    "mickey_error_string": (c_char_p, [c_int]),
+    "mickey_tables": (None, [c_void_p]),
+    "mickey_ops_per_clock": (c_int, [c_int]),
+    "mickey_version": (c_char_p, []),
+    "mickey_probe_lop3": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+}
+
+
+class MickeyError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__("mickey error %d: %s" % (code, message))
+        self.code = code
+        self.message = message
+
+
+def lib():
+    """Load libmickey.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    "libmickey.so is not built (%s); run `python -m "
+                    "paper_1909_04750_gb300.build` or __graft_entry__.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> MickeyError:
+    L = lib()
+    code = L.mickey_last_error()
+    msg = L.mickey_last_error_message()
+    return MickeyError(code, msg.decode() if msg else "")
+
+
+def check(rc: int) -> int:
+    if rc != OK:
+        raise last_error()
+    return rc
+
+
+def check_ptr(p):
+    if not p:
+        raise last_error()
+    return p

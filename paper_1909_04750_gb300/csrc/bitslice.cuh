@@ -1,0 +1,112 @@
+// Bitsliced MICKEY 2.0 clock and bit-matrix transpose (device code).
+//
+// Representation (Sec. IV-A): r[i] / s[i] is a 32-bit word whose bit l is
+// register bit i of lane l, so one thread clocks 32 instances at once with
+// full-width logic (Sec. IV-D: 200 words, 32 keystream bits per clock).
+//
+// The shift of each register is not executed: new word i is computed from
+// old words i-1, i, i+1 directly (register renaming, Sec. IV-C), and every
+// table constant is a compile-time value, so each register bit costs one
+// LOP3, plus one XOR where feedback enters.
+#pragma once
+
+#include <cstdint>
+
+#include "tables.cuh"
+
+namespace mickey {
+
+// Feedback contribution to S'_i: FB0_i & fb when CONTROL_BIT_S = 0 and
+// FB1_i & fb when it is 1, i.e. one of {0, fb, fb&~cbs, fb&cbs}.
+template <int I>
+__device__ __forceinline__ uint32_t s_feedback(uint32_t fb, uint32_t f0,
+                                               uint32_t f1) {
+  if constexpr (fb0(I) && fb1(I))
+    return fb;
+  else if constexpr (fb0(I))
+    return f0;
+  else if constexpr (fb1(I))
+    return f1;
+  else
+    return 0u;
+}
+
+// One bitsliced CLOCK_KG for 32 lanes.
+//   MIX   mixing mode (key/IV loading and preclocks): the R input takes
+//         in ^ s50, both feedbacks take `in` (bit l = input bit of lane l).
+//   MASK  lanes whose bit in `act` is 0 keep their old state (used while
+//         lanes with shorter IVs have not started their IV clocks yet).
+// Both registers are clocked from the old state (control bits
+// CONTROL_BIT_R = s34 ^ r67, CONTROL_BIT_S = s67 ^ r33).
+template <bool MIX, bool MASK>
+__device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
+                                         uint32_t (&s)[kReg], uint32_t in,
+                                         uint32_t act) {
+  const uint32_t cbr = s[34] ^ r[67];
+  uint32_t fbr = r[99];
+  uint32_t fbs = s[99];
+  if constexpr (MIX) {
+    fbr = fbr ^ in ^ s[50];
+    fbs = fbs ^ in;
+  }
+  const uint32_t cbs = s[67] ^ r[33];
+  const uint32_t f0 = fbs & ~cbs;
+  const uint32_t f1 = fbs & cbs;
+
+  uint32_t nr[kReg], ns[kReg];
+  // CLOCK_R: r'_i = r_{i-1} ^ (cbr & r_i) ^ (i in RTAPS ? fb : 0), r_{-1} = 0
+  nr[0] = (cbr & r[0]) ^ fbr;
+  static_for<1, kReg>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    uint32_t v = r[i - 1] ^ (cbr & r[i]);
+    if constexpr (rtap(i)) v ^= fbr;
+    nr[i] = v;
+  });
+  // CLOCK_S: s^_i = s_{i-1} ^ ((s_i ^ COMP0_i) & (s_{i+1} ^ COMP1_i)),
+  // s^_0 = 0, s^_99 = s_98, then the FB0/FB1 feedback.
+  ns[0] = fbs;
+  static_for<1, kReg - 1>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    constexpr uint32_t c0 = comp0(i) ? ~0u : 0u;
+    constexpr uint32_t c1 = comp1(i) ? ~0u : 0u;
+    uint32_t v = s[i - 1] ^ ((s[i] ^ c0) & (s[i + 1] ^ c1));
+    if constexpr (fb0(i) || fb1(i)) v ^= s_feedback<i>(fbs, f0, f1);
+    ns[i] = v;
+  });
+  ns[kReg - 1] = s[kReg - 2] ^ s_feedback<kReg - 1>(fbs, f0, f1);
+
+  static_for<0, kReg>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    if constexpr (MASK) {
+      r[i] = (nr[i] & act) | (r[i] & ~act);
+      s[i] = (ns[i] & act) | (s[i] & ~act);
+    } else {
+      r[i] = nr[i];
+      s[i] = ns[i];
+    }
+  });
+}
+
+// In-register transpose of a 32 x 32 bit matrix.  Row k is a[k]; column c
+// is bit (31 - c).  Afterwards a[c] bit (31 - k) equals the old a[k] bit
+// (31 - c).  Five stages swap the off-diagonal blocks of size 16, 8, 4, 2, 1.
+__device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+  auto stage = [&](auto jc, uint32_t m) {
+    constexpr int j = decltype(jc)::value;
+    static_for<0, 32>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr ((k & j) == 0) {
+        const uint32_t t = (a[k] ^ (a[k + j] >> j)) & m;
+        a[k] ^= t;
+        a[k + j] ^= t << j;
+      }
+    });
+  };
+  stage(std::integral_constant<int, 16>{}, 0x0000FFFFu);
+  stage(std::integral_constant<int, 8>{}, 0x00FF00FFu);
+  stage(std::integral_constant<int, 4>{}, 0x0F0F0F0Fu);
+  stage(std::integral_constant<int, 2>{}, 0x33333333u);
+  stage(std::integral_constant<int, 1>{}, 0x55555555u);
+}
+
+}  // namespace mickey

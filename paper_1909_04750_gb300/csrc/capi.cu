@@ -1,0 +1,462 @@
+// Host side of the C ABI declared in include/mickey.h: argument checking,
+// device memory of a handle, kernel launches, chunked device-to-host
+// generation, checkpoint export/import and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mickey.h"
+#include "internal.h"
+#include "tables.cuh"
+
+using namespace mickey;
+
+struct mickey_streams {
+  size_t n = 0;
+  uint32_t G = 0, Gpad = 0;
+  uint32_t *d_state = nullptr;    // kStateRows x Gpad
+  uint32_t *d_scratch = nullptr;  // (kScratchRows + 1) x Gpad
+  uint8_t *d_inputs = nullptr;    // staging for host inputs: keys, ivs, lens
+  int *d_err = nullptr;
+  cudaStream_t stream = nullptr;
+  int unroll = 4;
+  std::vector<uint64_t> pos;
+  // device staging for mickey_generate_host
+  void *d_stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+thread_local int t_err = MICKEY_OK;
+thread_local char t_msg[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+  t_err = code;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_msg, sizeof t_msg, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int ok() {
+  t_err = MICKEY_OK;
+  t_msg[0] = '\0';
+  return MICKEY_OK;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? MICKEY_E_OOM : MICKEY_E_CUDA,
+              "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call, what)                     \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+int default_unroll() {
+  const char *v = getenv("MICKEY_UNROLL");
+  if (v) {
+    const int u = atoi(v);
+    for (int k : kUnrolls)
+      if (k == u) return u;
+  }
+  return 4;
+}
+
+bool layout_ok(int layout) {
+  return layout >= MICKEY_LAYOUT_BITSLICED_U32 && layout <= MICKEY_LAYOUT_U32_F32;
+}
+
+// Output bytes of one call; 0 if the layout cannot hold n_bits.
+size_t out_bytes(size_t n, uint64_t n_bits, int layout) {
+  const uint64_t G = (n + 31) / 32;
+  switch (layout) {
+    case MICKEY_LAYOUT_BITSLICED_U32: return size_t(G * n_bits * 4);
+    case MICKEY_LAYOUT_BYTES: return size_t(n * ((n_bits + 7) / 8));
+    case MICKEY_LAYOUT_U32: return n_bits % 32 ? 0 : size_t(n * (n_bits / 8));
+    case MICKEY_LAYOUT_U32_F32: return n_bits % 32 ? 0 : size_t(2 * n * (n_bits / 8));
+    default: return 0;
+  }
+}
+
+void release(mickey_streams *s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->copy_stream) {
+    cudaStreamSynchronize(s->copy_stream);
+    cudaStreamDestroy(s->copy_stream);
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (s->ev_gen[k]) cudaEventDestroy(s->ev_gen[k]);
+    if (s->ev_copy[k]) cudaEventDestroy(s->ev_copy[k]);
+    if (s->d_stage[k]) cudaFree(s->d_stage[k]);
+  }
+  cudaFree(s->d_state);
+  cudaFree(s->d_scratch);
+  cudaFree(s->d_inputs);
+  cudaFree(s->d_err);
+  delete s;
+}
+
+int allocate(mickey_streams *s, size_t n) {
+  s->n = n;
+  s->G = uint32_t((n + 31) / 32);
+  s->Gpad = (s->G + 31u) & ~31u;
+  s->pos.assign(n, 0);
+  s->unroll = default_unroll();
+  CUDA_TRY(cudaMalloc(&s->d_state, size_t(kStateRows) * s->Gpad * 4), "cudaMalloc(state)");
+  CUDA_TRY(cudaMalloc(&s->d_scratch, size_t(kScratchRows + 1) * s->Gpad * 4),
+           "cudaMalloc(scratch)");
+  CUDA_TRY(cudaMalloc(&s->d_err, sizeof(int)), "cudaMalloc(err)");
+  CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream), "cudaMemset(err)");
+  return ok();
+}
+
+// Key/IV loading + preclock for all instances of s.
+int run_init(mickey_streams *s, const void *keys, const void *ivs,
+             const uint32_t *iv_lens, int mem) {
+  if (!keys || !ivs) return fail(MICKEY_E_ARG, "keys and ivs must not be NULL");
+  if (mem != MICKEY_MEM_HOST && mem != MICKEY_MEM_DEVICE)
+    return fail(MICKEY_E_ARG, "mem must be MICKEY_MEM_HOST or MICKEY_MEM_DEVICE");
+  const size_t n = s->n;
+  const uint8_t *dk, *di;
+  const uint32_t *dl = nullptr;
+  if (mem == MICKEY_MEM_HOST) {
+    if (iv_lens)
+      for (size_t i = 0; i < n; ++i)
+        if (iv_lens[i] > MICKEY_MAX_IV_BITS)
+          return fail(MICKEY_E_IVLEN, "iv_lens[%zu] = %u exceeds 80 bits", i, iv_lens[i]);
+    if (!s->d_inputs)
+      CUDA_TRY(cudaMalloc(&s->d_inputs, n * 24), "cudaMalloc(inputs)");
+    uint8_t *p = s->d_inputs;
+    CUDA_TRY(cudaMemcpyAsync(p, keys, n * 10, cudaMemcpyHostToDevice, s->stream), "H2D keys");
+    CUDA_TRY(cudaMemcpyAsync(p + n * 10, ivs, n * 10, cudaMemcpyHostToDevice, s->stream),
+             "H2D ivs");
+    dk = p;
+    di = p + n * 10;
+    if (iv_lens) {
+      // 4-byte aligned slot after the 20n bytes of keys and IVs
+      uint32_t *lens = reinterpret_cast<uint32_t *>(p + n * 20);
+      CUDA_TRY(cudaMemcpyAsync(lens, iv_lens, n * 4, cudaMemcpyHostToDevice, s->stream),
+               "H2D iv_lens");
+      dl = lens;
+    }
+  } else {
+    dk = static_cast<const uint8_t *>(keys);
+    di = static_cast<const uint8_t *>(ivs);
+    dl = iv_lens;
+  }
+  LoadArgs la{dk, di, dl, n, s->G, s->Gpad, s->d_scratch, s->d_err};
+  CUDA_TRY(launch_load(la, s->stream), "load_kernel launch");
+  PreclockArgs pa{s->d_scratch, s->d_state, s->G, s->Gpad};
+  CUDA_TRY(launch_preclock(pa, s->stream), "preclock_kernel launch");
+  std::fill(s->pos.begin(), s->pos.end(), 0);
+  return ok();
+}
+
+int check_limit(const mickey_streams *s, uint64_t n_bits) {
+  for (size_t i = 0; i < s->n; ++i)
+    if (s->pos[i] + n_bits > MICKEY_MAX_STREAM_BITS)
+      return fail(MICKEY_E_LIMIT,
+                  "stream %zu would pass 2^40 keystream bits (at %llu, +%llu)", i,
+                  (unsigned long long)s->pos[i], (unsigned long long)n_bits);
+  return MICKEY_OK;
+}
+
+int check_generate(const mickey_streams *s, uint64_t n_bits, const void *out, int layout) {
+  if (!s || !out) return fail(MICKEY_E_ARG, "handle and output must not be NULL");
+  if (n_bits == 0) return fail(MICKEY_E_ARG, "n_bits must be > 0");
+  if (!layout_ok(layout)) return fail(MICKEY_E_LAYOUT, "unknown layout %d", layout);
+  if ((layout == MICKEY_LAYOUT_U32 || layout == MICKEY_LAYOUT_U32_F32) && n_bits % 32)
+    return fail(MICKEY_E_LAYOUT, "u32 layouts need n_bits %% 32 == 0 (got %llu)",
+                (unsigned long long)n_bits);
+  return check_limit(s, n_bits);
+}
+
+// One keystream launch of `bits` clocks into a device buffer.
+int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
+  KeystreamArgs ka{s->d_state, s->G, s->Gpad, s->n, bits, out};
+  CUDA_TRY(launch_keystream(ka, layout, s->unroll, s->stream), "keystream_kernel launch");
+  return MICKEY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mickey_streams *mickey_init_streams(const uint8_t *keys, const uint8_t *ivs,
+                                    const uint32_t *iv_lens, size_t n) {
+  return mickey_init_streams_ex(keys, ivs, iv_lens, n, MICKEY_MEM_HOST, nullptr);
+}
+
+mickey_streams *mickey_init_streams_ex(const void *keys, const void *ivs,
+                                       const uint32_t *iv_lens, size_t n, int mem,
+                                       void *cuda_stream) {
+  if (!keys || !ivs || n == 0) {
+    fail(MICKEY_E_ARG, "keys/ivs must not be NULL and n must be > 0");
+    return nullptr;
+  }
+  if (n > (size_t(1) << 36)) {
+    fail(MICKEY_E_ARG, "n = %zu instances is above the supported 2^36", n);
+    return nullptr;
+  }
+  if (mem == MICKEY_MEM_HOST && iv_lens) {
+    for (size_t i = 0; i < n; ++i)
+      if (iv_lens[i] > MICKEY_MAX_IV_BITS) {
+        fail(MICKEY_E_IVLEN, "iv_lens[%zu] = %u exceeds 80 bits", i, iv_lens[i]);
+        return nullptr;
+      }
+  }
+  mickey_streams *s = new (std::nothrow) mickey_streams;
+  if (!s) {
+    fail(MICKEY_E_OOM, "host allocation failed");
+    return nullptr;
+  }
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (allocate(s, n) != MICKEY_OK || run_init(s, keys, ivs, iv_lens, mem) != MICKEY_OK) {
+    const int code = t_err;
+    char msg[512];
+    memcpy(msg, t_msg, sizeof msg);
+    release(s);
+    fail(code, "%s", msg);
+    return nullptr;
+  }
+  ok();
+  return s;
+}
+
+int mickey_reset_streams(mickey_streams *s, const void *keys, const void *ivs,
+                         const uint32_t *iv_lens, int mem) {
+  if (!s) return fail(MICKEY_E_ARG, "handle must not be NULL");
+  return run_init(s, keys, ivs, iv_lens, mem);
+}
+
+int mickey_set_stream(mickey_streams *s, void *cuda_stream) {
+  if (!s) return fail(MICKEY_E_ARG, "handle must not be NULL");
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  return ok();
+}
+
+int mickey_generate(mickey_streams *s, uint64_t n_bits, void *out, int layout) {
+  int rc = check_generate(s, n_bits, out, layout);
+  if (rc) return rc;
+  if (n_bits > kMaxBitsPerCall)
+    return fail(MICKEY_E_ARG, "n_bits per call is limited to 2^34 (got %llu)",
+                (unsigned long long)n_bits);
+  rc = launch_generate(s, n_bits, out, layout);
+  if (rc) return rc;
+  for (auto &p : s->pos) p += n_bits;
+  return ok();
+}
+
+size_t mickey_output_bytes(size_t n, uint64_t n_bits, int layout) {
+  return out_bytes(n, n_bits, layout);
+}
+
+int mickey_generate_host(mickey_streams *s, uint64_t n_bits, void *host_out, int layout) {
+  int rc = check_generate(s, n_bits, host_out, layout);
+  if (rc) return rc;
+  // Chunk of keystream bits per launch: a multiple of 32 giving about
+  // 256 MiB of output, so that two staging buffers stay small and copies
+  // overlap with generation.
+  const size_t per_bit = std::max<size_t>(1, out_bytes(s->n, 32, layout) / 32);
+  uint64_t chunk = (uint64_t(256) << 20) / per_bit;
+  chunk = std::max<uint64_t>(32, chunk & ~uint64_t(31));
+  chunk = std::min<uint64_t>(chunk, (n_bits + 31) & ~uint64_t(31));
+  const size_t need = out_bytes(s->n, chunk, layout);
+  if (s->stage_bytes < need) {
+    for (int k = 0; k < 2; ++k) {
+      if (s->d_stage[k]) cudaFree(s->d_stage[k]);
+      s->d_stage[k] = nullptr;
+    }
+    s->stage_bytes = 0;
+    for (int k = 0; k < 2; ++k) CUDA_TRY(cudaMalloc(&s->d_stage[k], need), "cudaMalloc(stage)");
+    s->stage_bytes = need;
+  }
+  if (!s->copy_stream) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking),
+             "cudaStreamCreate");
+    for (int k = 0; k < 2; ++k) {
+      CUDA_TRY(cudaEventCreateWithFlags(&s->ev_gen[k], cudaEventDisableTiming), "event");
+      CUDA_TRY(cudaEventCreateWithFlags(&s->ev_copy[k], cudaEventDisableTiming), "event");
+    }
+  }
+  uint8_t *host = static_cast<uint8_t *>(host_out);
+  const uint64_t G = s->G;
+  uint64_t done = 0;
+  int k = 0;
+  while (done < n_bits) {
+    const uint64_t bits = std::min<uint64_t>(chunk, n_bits - done);
+    void *buf = s->d_stage[k];
+    CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_copy[k], 0), "wait copy");
+    rc = launch_generate(s, bits, buf, layout);
+    if (rc) return rc;
+    CUDA_TRY(cudaEventRecord(s->ev_gen[k], s->stream), "record");
+    CUDA_TRY(cudaStreamWaitEvent(s->copy_stream, s->ev_gen[k], 0), "wait gen");
+    // copy the chunk's rows into their columns of the full host array
+    switch (layout) {
+      case MICKEY_LAYOUT_BITSLICED_U32:
+        CUDA_TRY(cudaMemcpy2DAsync(host + done * 4, n_bits * 4, buf, bits * 4, bits * 4, G,
+                                   cudaMemcpyDeviceToHost, s->copy_stream), "D2H");
+        break;
+      case MICKEY_LAYOUT_BYTES:
+        CUDA_TRY(cudaMemcpy2DAsync(host + done / 8, (n_bits + 7) / 8, buf, (bits + 7) / 8,
+                                   (bits + 7) / 8, s->n, cudaMemcpyDeviceToHost,
+                                   s->copy_stream), "D2H");
+        break;
+      default: {
+        const size_t w = bits / 8, W = n_bits / 8;  // bytes per row
+        CUDA_TRY(cudaMemcpy2DAsync(host + done / 8, W, buf, w, w, s->n,
+                                   cudaMemcpyDeviceToHost, s->copy_stream), "D2H");
+        if (layout == MICKEY_LAYOUT_U32_F32)
+          CUDA_TRY(cudaMemcpy2DAsync(host + s->n * W + done / 8, W,
+                                     static_cast<uint8_t *>(buf) + s->n * w, w, w, s->n,
+                                     cudaMemcpyDeviceToHost, s->copy_stream), "D2H");
+      }
+    }
+    CUDA_TRY(cudaEventRecord(s->ev_copy[k], s->copy_stream), "record");
+    for (auto &p : s->pos) p += bits;
+    done += bits;
+    k ^= 1;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s->copy_stream), "sync copy");
+  return ok();
+}
+
+int mickey_sync(mickey_streams *s) {
+  if (!s) return fail(MICKEY_E_ARG, "handle must not be NULL");
+  CUDA_TRY(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+  int flag = 0;
+  CUDA_TRY(cudaMemcpy(&flag, s->d_err, sizeof flag, cudaMemcpyDeviceToHost), "D2H err");
+  if (flag) {
+    CUDA_TRY(cudaMemset(s->d_err, 0, sizeof(int)), "clear err");
+    if (flag & kErrIvLen) return fail(MICKEY_E_IVLEN, "an IV length above 80 bits was given");
+    if (flag & kErrTimeout) return fail(MICKEY_E_TIMEOUT, "a device-side wait timed out");
+  }
+  return ok();
+}
+
+size_t mickey_num_streams(const mickey_streams *s) { return s ? s->n : 0; }
+
+uint64_t mickey_position(const mickey_streams *s, size_t i) {
+  if (!s || i >= s->n) return UINT64_MAX;
+  return s->pos[i];
+}
+
+int mickey_export_state(mickey_streams *s, uint8_t *states, uint64_t *positions) {
+  if (!s || !states) return fail(MICKEY_E_ARG, "handle and states must not be NULL");
+  std::vector<uint32_t> words(size_t(kStateRows) * s->Gpad);
+  CUDA_TRY(cudaStreamSynchronize(s->stream), "sync");
+  CUDA_TRY(cudaMemcpy(words.data(), s->d_state, words.size() * 4, cudaMemcpyDeviceToHost),
+           "D2H state");
+  for (size_t i = 0; i < s->n; ++i) {
+    const size_t g = i / 32, l = i % 32;
+    uint8_t *rec = states + 26 * i;
+    memset(rec, 0, 26);
+    for (int half = 0; half < 2; ++half)
+      for (int b = 0; b < kReg; ++b) {
+        const uint32_t w = words[size_t(half * kReg + b) * s->Gpad + g];
+        if ((w >> l) & 1u) rec[13 * half + b / 8] |= uint8_t(0x80u >> (b % 8));
+      }
+    if (positions) positions[i] = s->pos[i];
+  }
+  return ok();
+}
+
+mickey_streams *mickey_import_state(const uint8_t *states, const uint64_t *positions,
+                                    size_t n, void *cuda_stream) {
+  if (!states || n == 0) {
+    fail(MICKEY_E_ARG, "states must not be NULL and n must be > 0");
+    return nullptr;
+  }
+  mickey_streams *s = new (std::nothrow) mickey_streams;
+  if (!s) {
+    fail(MICKEY_E_OOM, "host allocation failed");
+    return nullptr;
+  }
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (allocate(s, n) != MICKEY_OK) {
+    const int code = t_err;
+    release(s);
+    t_err = code;
+    return nullptr;
+  }
+  std::vector<uint32_t> words(size_t(kStateRows) * s->Gpad, 0u);
+  for (size_t i = 0; i < n; ++i) {
+    const size_t g = i / 32, l = i % 32;
+    const uint8_t *rec = states + 26 * i;
+    for (int half = 0; half < 2; ++half)
+      for (int b = 0; b < kReg; ++b)
+        if ((rec[13 * half + b / 8] >> (7 - b % 8)) & 1u)
+          words[size_t(half * kReg + b) * s->Gpad + g] |= 1u << l;
+    if (positions) {
+      if (positions[i] > MICKEY_MAX_STREAM_BITS) {
+        release(s);
+        fail(MICKEY_E_LIMIT, "position of stream %zu is beyond 2^40", i);
+        return nullptr;
+      }
+      s->pos[i] = positions[i];
+    }
+  }
+  cudaError_t e = cudaMemcpy(s->d_state, words.data(), words.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    release(s);
+    cuda_fail(e, "H2D state");
+    return nullptr;
+  }
+  ok();
+  return s;
+}
+
+void mickey_free(mickey_streams *s) { release(s); }
+
+int mickey_last_error(void) { return t_err; }
+const char *mickey_last_error_message(void) { return t_msg; }
+
+const char *mickey_error_string(int code) {
+  switch (code) {
+    case MICKEY_OK: return "ok";
+    case MICKEY_E_ARG: return "invalid argument";
+    case MICKEY_E_IVLEN: return "IV length above 80 bits";
+    case MICKEY_E_LIMIT: return "more than 2^40 keystream bits for one key/IV";
+    case MICKEY_E_LAYOUT: return "invalid layout for this request";
+    case MICKEY_E_OOM: return "out of memory";
+    case MICKEY_E_CUDA: return "CUDA error";
+    case MICKEY_E_TIMEOUT: return "device-side wait timed out";
+    case MICKEY_E_STATE: return "handle not usable for this call";
+    default: return "unknown error";
+  }
+}
+
+void mickey_tables(uint32_t masks[5][4]) {
+  memset(masks, 0, sizeof(uint32_t) * 20);
+  static_for<0, kReg>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    constexpr uint32_t bit = 1u << (i % 32);
+    if constexpr (rtap(i)) masks[0][i / 32] |= bit;
+    if constexpr (comp0(i)) masks[1][i / 32] |= bit;
+    if constexpr (comp1(i)) masks[2][i / 32] |= bit;
+    if constexpr (fb0(i)) masks[3][i / 32] |= bit;
+    if constexpr (fb1(i)) masks[4][i / 32] |= bit;
+  });
+}
+
+int mickey_ops_per_clock(int mixing) {
+  constexpr int keystream = ops_per_clock(false), init = ops_per_clock(true);
+  return mixing ? init : keystream;
+}
+
+const char *mickey_version(void) { return "mickey-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal interfaces between the C ABI (capi.cu) and the kernel
+// translation units.  Plain pointers and sizes only.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace mickey {
+
+// Device-side error bits, OR-ed into a per-handle flag word.
+constexpr int kErrIvLen = 1;
+constexpr int kErrTimeout = 2;
+
+// Rows of the bitsliced input scratch, each Gpad words long:
+//   [0, 80)    key words K[j], bit l = key bit j of lane l
+//   [80, 160)  IV-phase input words, right-aligned per lane
+//   [160, 240) IV-phase activity masks (only read for mixed-length groups)
+// followed by one info word per group: max IV length | (mixed << 8).
+constexpr int kKeyRow = 0;
+constexpr int kIvRow = 80;
+constexpr int kActRow = 160;
+constexpr int kScratchRows = 240;
+
+// Bitsliced state: 200 rows of Gpad words, r0..r99 then s0..s99.
+constexpr int kStateRows = 200;
+
+constexpr int kInitThreads = 128;
+
+struct LoadArgs {
+  const uint8_t *keys;      // n x 10, device
+  const uint8_t *ivs;       // n x 10, device
+  const uint32_t *iv_lens;  // n, device, or nullptr (= 80)
+  uint64_t n;
+  uint32_t G, Gpad;
+  uint32_t *scratch;        // kScratchRows * Gpad + Gpad words
+  int *err;
+};
+
+struct PreclockArgs {
+  const uint32_t *scratch;
+  uint32_t *state;          // kStateRows * Gpad words
+  uint32_t G, Gpad;
+};
+
+cudaError_t launch_load(const LoadArgs &a, cudaStream_t st);
+cudaError_t launch_preclock(const PreclockArgs &a, cudaStream_t st);
+
+struct KeystreamArgs {
+  uint32_t *state;          // kStateRows * Gpad words, read and written back
+  uint32_t G, Gpad;
+  uint64_t n;               // instances
+  uint64_t n_bits;          // keystream bits per instance in this call
+  void *out;                // device output, layout-dependent
+};
+
+// Unroll factors compiled for the keystream kernel.
+constexpr int kUnrolls[] = {2, 4};
+// Largest n_bits of one keystream launch: a row of the row-major layouts
+// must stay below 4 GiB.
+constexpr uint64_t kMaxBitsPerCall = 1ull << 34;
+constexpr int kKsThreads = 128;
+
+cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll,
+                             cudaStream_t st);
+
+}  // namespace mickey

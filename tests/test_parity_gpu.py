@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA path through the C ABI against the scalar oracle.
+
+The cipher is deterministic, so every comparison is exact (tolerance 0).
+Small cases are compared on every instance and bit; the full-size workloads
+(2^20 x 2^14 and 2^24 x 2^12 bits) are compared on sampled instances that
+always include the first and the last group, plus properties checked on the
+whole output.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_04750_gb300 import _native as N
+from paper_1909_04750_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_04750_gb300 import build as B
+    B.build()
+    N.lib()
+
+
+def _streams(s):
+    from paper_1909_04750_gb300.streams import Streams
+    return Streams(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda(),
+                   torch.from_numpy(s.iv_lens.astype(np.int32)).cuda())
+
+
+def _ref(s, n_bits):
+    return oracle.batch_bytes(s.keys, s.ivs, s.iv_lens, n_bits, threads=THREADS)
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _first_diff(a, b):
+    rows = np.nonzero(np.any(a != b, axis=tuple(range(1, a.ndim))))[0]
+    return None if rows.size == 0 else int(rows[0])
+
+
+# -------------------------------------------------------------- plain, small
+
+def test_plain_small_bitsliced_full():
+    s = workloads.plain_small()
+    ref = _ref(s, 65536)
+    st = _streams(s)
+    got = _u32(st.generate(65536, "bitsliced"))
+    st.sync()
+    assert _first_diff(got, oracle.to_bitsliced(ref, 65536)) is None
+
+
+def test_plain_small_bytes_full():
+    s = workloads.plain_small()
+    ref = _ref(s, 65536)
+    st = _streams(s)
+    got = st.generate(65536, "bytes").cpu().numpy()
+    st.sync()
+    assert _first_diff(got, ref) is None
+
+
+@pytest.mark.parametrize("n,n_bits", [(1, 8), (1, 40), (33, 96), (45, 77), (64, 1000),
+                                      (100, 4096), (31, 33)])
+def test_ragged_sizes_all_layouts(n, n_bits):
+    s = workloads.plain_scale(n)
+    ref = _ref(s, n_bits)
+    st = _streams(s)
+    got = _u32(st.generate(n_bits, "bitsliced"))
+    assert _first_diff(got, oracle.to_bitsliced(ref, n_bits)) is None
+    st.reset(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
+    got = st.generate(n_bits, "bytes").cpu().numpy()
+    assert _first_diff(got, ref) is None
+    if n_bits % 32 == 0:
+        st.reset(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
+        u = _u32(st.generate(n_bits, "u32"))
+        assert _first_diff(u, oracle.to_u32(ref, n_bits)) is None
+        st.reset(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
+        both = st.generate(n_bits, "u32_f32").cpu().numpy()
+        assert _first_diff(both[0].view(np.uint32), oracle.to_u32(ref, n_bits)) is None
+        f = both[1].view(np.float32)
+        assert np.array_equal(f, oracle.to_f32(oracle.to_u32(ref, n_bits)))
+    st.sync()
+
+
+def test_mixed_iv_lengths_in_one_group():
+    # every IV length 0..80 appears, many inside the same 32-lane groups
+    s = workloads.batched(162)
+    s.iv_lens[:] = np.arange(162) % 81
+    ref = _ref(s, 512)
+    st = _streams(s)
+    got = st.generate(512, "bytes").cpu().numpy()
+    st.sync()
+    assert _first_diff(got, ref) is None
+
+
+def test_batched_workload_iv_lengths_sampled():
+    s = workloads.batched(4096)
+    ref = _ref(s, 256)
+    st = _streams(s)
+    got = st.generate(256, "bytes").cpu().numpy()
+    st.sync()
+    assert _first_diff(got, ref) is None
+
+
+def test_host_input_path():
+    from paper_1909_04750_gb300.streams import Streams
+    s = workloads.batched(70)
+    st = Streams(s.keys, s.ivs, s.iv_lens)   # numpy: host-memory inputs
+    got = st.generate(200, "bytes").cpu().numpy()
+    st.sync()
+    assert _first_diff(got, _ref(s, 200)) is None
+
+
+# -------------------------------------------------------------- continuation
+
+def test_resume_split_equals_contiguous():
+    s = workloads.plain_scale(70)
+    st = _streams(s)
+    a = _u32(st.generate(137, "bitsliced"))
+    b = _u32(st.generate(1000, "bitsliced"))
+    c = _u32(st.generate(32, "bitsliced"))
+    st.sync()
+    assert st.position(0) == 1169
+    whole = oracle.to_bitsliced(_ref(s, 1169), 1169)
+    assert np.array_equal(np.concatenate([a, b, c], axis=1), whole)
+
+
+def test_export_import_resume():
+    from paper_1909_04750_gb300.streams import Streams
+    s = workloads.plain_scale(50)
+    st = _streams(s)
+    first = st.generate(64, "bytes").cpu().numpy()
+    states, pos = st.export_state()
+    assert np.all(pos == 64)
+    st2 = Streams.import_state(states, pos)
+    rest = st2.generate(192, "bytes").cpu().numpy()
+    st2.sync()
+    assert st2.position(49) == 256
+    assert np.array_equal(np.concatenate([first, rest], axis=1), _ref(s, 256))
+
+
+def test_export_state_matches_oracle_state():
+    s = workloads.plain_scale(40)
+    st = _streams(s)
+    st.generate(77, "bitsliced")
+    states, _ = st.export_state()
+    for i in (0, 17, 39):
+        ost = oracle.init(s.keys[i].tobytes(), s.ivs[i].tobytes(), int(s.iv_lens[i]))
+        oracle.keystream_from(ost, 77)
+        r, sb = ost.bits()
+        rec = np.concatenate([np.packbits(r), np.packbits(sb)])
+        assert np.array_equal(states[i], rec)
+
+
+def test_generate_host_matches_device():
+    s = workloads.plain_scale(96)
+    st = _streams(s)
+    dev = _u32(st.generate(2048, "bitsliced"))
+    host = st.generate_host(4096, "bytes").numpy()
+    host_u = st.generate_host(1024, "u32_f32").numpy()
+    st.sync()
+    ref = _ref(s, 2048 + 4096 + 1024)
+    assert np.array_equal(dev, oracle.to_bitsliced(ref, 2048 + 4096 + 1024)[:, :2048])
+    assert np.array_equal(host, ref[:, 256:768])
+    u = oracle.to_u32(ref[:, 768:], 1024)
+    assert np.array_equal(host_u[0].view(np.uint32), u)
+    assert np.array_equal(host_u[1].view(np.float32), oracle.to_f32(u))
+
+
+# -------------------------------------------------------------- lanes
+
+def test_lane_independence():
+    s = workloads.plain_scale(64)
+    base = _streams(s).generate(512, "bytes").cpu().numpy()
+    k2 = s.keys.copy()
+    k2[37, 3] ^= 0x10
+    s2 = workloads.StreamSet("x", 0, k2, s.ivs, s.iv_lens, s.n_bits)
+    other = _streams(s2).generate(512, "bytes").cpu().numpy()
+    changed = np.nonzero(np.any(base != other, axis=1))[0]
+    assert changed.tolist() == [37]
+
+
+def test_device_iv_len_above_80_reported():
+    from paper_1909_04750_gb300.streams import Streams
+    s = workloads.plain_scale(40)
+    lens = torch.full((40,), 80, dtype=torch.int32, device="cuda")
+    lens[5] = 81
+    st = Streams(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda(), lens)
+    with pytest.raises(N.MickeyError) as ei:
+        st.sync()
+    assert ei.value.code == N.E_IVLEN
+    st.sync()  # the flag is cleared once reported
+
+
+def test_limit_2_pow_40_enforced():
+    from paper_1909_04750_gb300.streams import Streams
+    s = workloads.plain_scale(32)
+    st = _streams(s)
+    states, _ = st.export_state()
+    near = Streams.import_state(states, np.full(32, (1 << 40) - 64, np.uint64))
+    near.generate(64, "bitsliced")
+    with pytest.raises(N.MickeyError) as ei:
+        near.generate(32, "bitsliced")
+    assert ei.value.code == N.E_LIMIT
+
+
+# -------------------------------------------------------------- full size
+
+def _sample_rows(n, k, seed):
+    rng = np.random.default_rng(seed)
+    pick = set(range(32)) | set(range(n - 32, n)) | set(rng.integers(0, n, k).tolist())
+    return np.array(sorted(pick))
+
+
+def test_plain_scale_full_size_sampled():
+    s = workloads.plain_scale()
+    n_bits = int(s.n_bits[0])
+    st = _streams(s)
+    out = st.generate(n_bits, "bytes")
+    st.reset(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
+    bs = st.generate(n_bits, "bitsliced")
+    st.sync()
+    rows = _sample_rows(s.n, 1024, 11)
+    sub = s.subset(rows)
+    ref = _ref(sub, n_bits)
+    got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert _first_diff(got, ref) is None
+    # bitsliced layout: the sampled instances' lanes of their groups
+    groups = np.unique(rows // 32)
+    gbs = _u32(bs[torch.from_numpy(groups).cuda()])
+    for r in rows[:: max(1, len(rows) // 64)]:
+        gi = int(np.searchsorted(groups, r // 32))
+        lane = ((gbs[gi] >> np.uint32(r % 32)) & 1).astype(np.uint8)
+        assert np.array_equal(np.packbits(lane), ref[np.searchsorted(rows, r)])
+    # whole-output property: both layouts hold the same number of ones
+    ones_bytes = int(torch.bitwise_count(out.view(torch.int32)).sum()) if hasattr(
+        torch, "bitwise_count") else None
+    if ones_bytes is not None:
+        assert ones_bytes == int(torch.bitwise_count(bs).sum())
+    del out, bs
+    torch.cuda.empty_cache()
+
+
+def test_fused_full_size_sampled():
+    s = workloads.fused()
+    n_bits = int(s.n_bits[0])
+    st = _streams(s)
+    both = st.generate(n_bits, "u32_f32")
+    st.sync()
+    u = both[0]
+    f = both[1].view(torch.float32)
+    # property on every output word: f == (u >> 8) * 2^-24, exactly
+    chk = (u.view(torch.int32) >> 8) & 0xFFFFFF
+    assert bool(torch.equal(chk.to(torch.float32) * (2.0 ** -24), f))
+    rows = _sample_rows(s.n, 1024, 13)
+    ref = oracle.to_u32(_ref(s.subset(rows), n_bits), n_bits)
+    got = u[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.uint32)
+    assert _first_diff(got, ref) is None
+    del both, u, f, chk
+    torch.cuda.empty_cache()
