@@ -120,7 +120,8 @@ MICKEY_API int mickey_set_stream(mickey_streams *s, void *cuda_stream);
  * thread per clock).  Stateful: each call continues every stream where the
  * previous call stopped.  `out` is a caller-owned DEVICE buffer of
  * mickey_output_bytes(n, n_bits, layout) bytes.
- * Errors: MICKEY_E_ARG (s or out NULL, n_bits == 0), MICKEY_E_LAYOUT,
+ * Errors: MICKEY_E_ARG (s or out NULL, n_bits == 0 or above 2^34 per call,
+ * out not 4-byte aligned for a 32-bit layout), MICKEY_E_LAYOUT,
  * MICKEY_E_LIMIT (a stream would pass 2^40 bits), MICKEY_E_CUDA.
  * ------------------------------------------------------------------------ */
 MICKEY_API int mickey_generate(mickey_streams *s, uint64_t n_bits, void *out, int layout);

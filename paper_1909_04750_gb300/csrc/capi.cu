@@ -181,6 +181,8 @@ int check_generate(const mickey_streams *s, uint64_t n_bits, const void *out, in
   if ((layout == MICKEY_LAYOUT_U32 || layout == MICKEY_LAYOUT_U32_F32) && n_bits % 32)
     return fail(MICKEY_E_LAYOUT, "u32 layouts need n_bits %% 32 == 0 (got %llu)",
                 (unsigned long long)n_bits);
+  if (layout != MICKEY_LAYOUT_BYTES && reinterpret_cast<uintptr_t>(out) % 4)
+    return fail(MICKEY_E_ARG, "output of a 32-bit layout must be 4-byte aligned");
   return check_limit(s, n_bits);
 }
 
