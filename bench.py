@@ -29,20 +29,18 @@ METRIC = "keystream Gbit/s on 1 GB300 (bit-exact), % of int-LOP roofline; served
 WORKLOAD = ("plain_scale: 2^20 MICKEY 2.0 instances (32768 bitsliced groups), 80-bit keys "
             "and IVs from splitmix64 seed 2, 100 mixing preclocks, 2^14 keystream bits "
             "per instance, row-major bytes output (2 GiB)")
-# Integer-logic peak of the GB300: SMs x LOP3 results per SM per clock
-# (measured by mickey_probe_lop3) x the maximum SM clock.
+# Integer-logic peak of the GB300: 152 SMs x 64 LOP3 results per SM per
+# clock (measured with mickey_probe_lop3: 63.2-64.0 per SM-cycle over 1-8
+# resident blocks) x the maximum SM clock of 2070 MHz = 20.14 T ops/s.
 N_SM = 152
 SM_MAX_MHZ = 2070.0
-
-
-def lop3_per_sm_clk() -> float:
-    return float(os.environ.get("MICKEY_LOP3_PER_SM_CLK", "64"))
+LOP3_PER_SM_CLK = 64.0
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=1 << 20)
@@ -176,7 +174,7 @@ def main():
     import torch.distributed as dist
 
     from paper_1909_04750_gb300 import _native as N
-    from paper_1909_04750_gb300 import workloads
+    from paper_1909_04750_gb300 import autotune, workloads
     from paper_1909_04750_gb300.build import build
     from paper_1909_04750_gb300.streams import Streams, ops_per_clock
 
@@ -195,6 +193,10 @@ def main():
     st = Streams(keys, ivs, lens)
     out = torch.empty((n, n_bits // 8), dtype=torch.uint8, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+
+    # launch configuration from the autotuner (timed once per shape, cached)
+    tuned = autotune.tune(st, n_bits, N.LAYOUT_BYTES)
+    tuned_bs = autotune.tune(st, n_bits, N.LAYOUT_BITSLICED_U32)
 
     def step(layout="bytes", o=out):
         st.reset(keys, ivs, lens)
@@ -253,7 +255,7 @@ def main():
     ops = groups * n_bits * ops_per_clock(False)
     ks_avg_s = statistics.mean(ks_ms) * 1e-3
     achieved = ops / ks_avg_s / 1e12
-    peak = N_SM * lop3_per_sm_clk() * SM_MAX_MHZ * 1e6 / 1e12
+    peak = N_SM * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     init_ops = groups * 260 * ops_per_clock(True)
     whole_ops = ops + init_ops
 
@@ -298,16 +300,17 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "instances_per_gpu": n, "bits_per_instance": n_bits,
                        "layout": "bytes", "l2": "512 MiB buffer written between timed steps; "
-                       "output 2 GiB > L2"},
+                       "output 2 GiB > L2", "launch": autotune.describe(tuned),
+                       "launch_bitsliced": autotune.describe(tuned_bs)},
             "pct_int_lop_roofline": 100.0 * (whole_ops / (total_ms / args.steps * 1e-3) / 1e12)
                                     / peak,
             "bitsliced_u32_gbit_s": bs_value,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "keystream_kernel<bytes>",
+                         "kernel": "keystream kernel, bytes layout (%s)" % autotune.describe(tuned),
                          "ops_per_clock_per_group": ops_per_clock(False),
                          "peak_basis": "%d SMs x %g LOP3/SM/clk (mickey_probe_lop3) x %g MHz"
-                                       % (N_SM, lop3_per_sm_clk(), SM_MAX_MHZ)},
+                                       % (N_SM, LOP3_PER_SM_CLK, SM_MAX_MHZ)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,

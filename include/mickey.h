@@ -162,6 +162,40 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
                                     const uint64_t *positions, size_t n,
                                     void *cuda_stream);
 
+/* --------------------------------------------------------------------------
+ * Launch configuration and autotuning of the keystream kernel (per layout).
+ *   mode    MICKEY_MODE_GRID: one thread per 32-lane group, 4 warps per block;
+ *           MICKEY_MODE_PERSISTENT: one warp per SM sub-partition, the
+ *           groups x tiles work line cut into equal segments (used only when
+ *           there are at least as many 1024-instance warp-groups as warps);
+ *           MICKEY_MODE_AUTO: persistent when the grid launch would leave
+ *           much of its last wave empty.
+ *   unroll  clocks per inner step, 2 or 4.
+ *   stage   row layouts: stage four 32-bit words per row in shared memory
+ *           and write 16-byte chunks (needs n_bits % 128 == 0).
+ * ------------------------------------------------------------------------ */
+#define MICKEY_MODE_AUTO 0
+#define MICKEY_MODE_GRID 1
+#define MICKEY_MODE_PERSISTENT 2
+
+typedef struct {
+  int mode, unroll, stage;
+  float ms; /* best of two timed launches */
+} mickey_tune_result;
+
+MICKEY_API int mickey_set_config(mickey_streams *s, int layout, int mode, int unroll,
+                                 int stage);
+MICKEY_API int mickey_get_config(const mickey_streams *s, int layout, int *mode,
+                                 int *unroll, int *stage);
+
+/* Time every configuration on this handle's own streams for one call of
+ * n_bits in `layout` (the state is saved and restored: positions do not
+ * move), keep the fastest for that layout, and report each candidate in
+ * results[0 .. min(max_results, *n_results)).  Synchronous; allocates a
+ * temporary output buffer and a state copy.  results/n_results may be NULL. */
+MICKEY_API int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout,
+                           mickey_tune_result *results, int max_results, int *n_results);
+
 /* Synchronise, release all device memory of the handle.  NULL is a no-op. */
 MICKEY_API void mickey_free(mickey_streams *s);
 

@@ -17,6 +17,12 @@ OK = 0
 E_ARG, E_IVLEN, E_LIMIT, E_LAYOUT, E_OOM, E_CUDA, E_TIMEOUT, E_STATE = range(-1, -9, -1)
 LAYOUT_BITSLICED_U32, LAYOUT_BYTES, LAYOUT_U32, LAYOUT_U32_F32 = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE = 0, 1
+MODE_AUTO, MODE_GRID, MODE_PERSISTENT = 0, 1, 2
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("unroll", ctypes.c_int), ("stage", ctypes.c_int),
+                ("ms", ctypes.c_float)]
 MAX_STREAM_BITS = 1 << 40
 
 _lock = threading.Lock()
@@ -49,6 +55,9 @@ SIGNATURES = {
     "mickey_ops_per_clock": (c_int, [c_int]),
     "mickey_version": (c_char_p, []),
     "mickey_probe_lop3": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "mickey_set_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
+    "mickey_get_config": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "mickey_tune": (c_int, [c_void_p, c_uint64, c_int, c_void_p, c_int, c_void_p]),
 }
 
 

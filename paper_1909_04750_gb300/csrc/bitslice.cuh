@@ -34,8 +34,13 @@ __device__ __forceinline__ uint32_t s_feedback(uint32_t fb, uint32_t f0,
 // One bitsliced CLOCK_KG for 32 lanes.
 //   MIX   mixing mode (key/IV loading and preclocks): the R input takes
 //         in ^ s50, both feedbacks take `in` (bit l = input bit of lane l).
-//   MASK  lanes whose bit in `act` is 0 keep their old state (used while
-//         lanes with shorter IVs have not started their IV clocks yet).
+//   MASK  lanes whose bit in `act` is 0 keep their state.  Only used while
+//         lanes with shorter IVs have not started their IV clocks: such a
+//         lane's state is all zero and its input bits are zero, and a clock
+//         of the zero state with zero input changes nothing except the S
+//         positions i where COMP0_i = COMP1_i = 1 (s^_i gets c0 & c1 = 1),
+//         so AND-ing `act` into the non-linear term of exactly those
+//         positions keeps inactive lanes at zero.
 // Both registers are clocked from the old state (control bits
 // CONTROL_BIT_R = s34 ^ r67, CONTROL_BIT_S = s67 ^ r33).
 template <bool MIX, bool MASK>
@@ -69,7 +74,9 @@ __device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
     constexpr int i = decltype(ic)::value;
     constexpr uint32_t c0 = comp0(i) ? ~0u : 0u;
     constexpr uint32_t c1 = comp1(i) ? ~0u : 0u;
-    uint32_t v = s[i - 1] ^ ((s[i] ^ c0) & (s[i + 1] ^ c1));
+    uint32_t nl = (s[i] ^ c0) & (s[i + 1] ^ c1);
+    if constexpr (MASK && comp0(i) && comp1(i)) nl &= act;
+    uint32_t v = s[i - 1] ^ nl;
     if constexpr (fb0(i) || fb1(i)) v ^= s_feedback<i>(fbs, f0, f1);
     ns[i] = v;
   });
@@ -77,13 +84,8 @@ __device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
 
   static_for<0, kReg>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    if constexpr (MASK) {
-      r[i] = (nr[i] & act) | (r[i] & ~act);
-      s[i] = (ns[i] & act) | (s[i] & ~act);
-    } else {
-      r[i] = nr[i];
-      s[i] = ns[i];
-    }
+    r[i] = nr[i];
+    s[i] = ns[i];
   });
 }
 

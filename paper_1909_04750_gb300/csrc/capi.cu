@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -25,6 +26,17 @@ struct mickey_streams {
   int *d_err = nullptr;
   cudaStream_t stream = nullptr;
   int unroll = 4;
+  int mode = 0;                   // 0 auto, 1 grid, 2 persistent
+  bool stage = true;              // row layouts: 16-byte staged row stores
+  struct LayoutCfg {
+    bool set = false;
+    int mode = 0, unroll = 4;
+    bool stage = true;
+  } cfg[4];                       // per-layout settings (mickey_set_config / tune)
+  int sm_count = 0;
+  int persist_blocks = 0;         // blocks of the persistent kernel (<= SMs)
+  uint32_t *d_flags = nullptr;    // persistent mode: one word per warp-group
+  uint32_t epoch = 0;
   std::vector<uint64_t> pos;
   // device staging for mickey_generate_host
   void *d_stage[2] = {nullptr, nullptr};
@@ -63,6 +75,13 @@ int cuda_fail(cudaError_t e, const char *what) {
     cudaError_t e_ = (call);                     \
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
+
+int default_mode() {
+  const char *v = getenv("MICKEY_MODE");
+  if (v && !strcmp(v, "grid")) return MICKEY_MODE_GRID;
+  if (v && !strcmp(v, "persistent")) return MICKEY_MODE_PERSISTENT;
+  return MICKEY_MODE_AUTO;
+}
 
 int default_unroll() {
   const char *v = getenv("MICKEY_UNROLL");
@@ -106,6 +125,7 @@ void release(mickey_streams *s) {
   cudaFree(s->d_scratch);
   cudaFree(s->d_inputs);
   cudaFree(s->d_err);
+  cudaFree(s->d_flags);
   delete s;
 }
 
@@ -115,6 +135,20 @@ int allocate(mickey_streams *s, size_t n) {
   s->Gpad = (s->G + 31u) & ~31u;
   s->pos.assign(n, 0);
   s->unroll = default_unroll();
+  s->mode = default_mode();
+  if (const char *v = getenv("MICKEY_STAGE")) s->stage = atoi(v) != 0;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  CUDA_TRY(cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev),
+           "cudaDeviceGetAttribute");
+  s->persist_blocks = s->sm_count;
+  if (const char *v = getenv("MICKEY_PERSIST_BLOCKS")) {
+    const int b = atoi(v);
+    if (b > 0 && b < s->sm_count) s->persist_blocks = b;
+  }
+  CUDA_TRY(cudaMalloc(&s->d_flags, size_t((s->G + 31) / 32) * 4), "cudaMalloc(flags)");
+  CUDA_TRY(cudaMemsetAsync(s->d_flags, 0, size_t((s->G + 31) / 32) * 4, s->stream),
+           "cudaMemset(flags)");
   CUDA_TRY(cudaMalloc(&s->d_state, size_t(kStateRows) * s->Gpad * 4), "cudaMalloc(state)");
   CUDA_TRY(cudaMalloc(&s->d_scratch, size_t(kScratchRows + 1) * s->Gpad * 4),
            "cudaMalloc(scratch)");
@@ -186,10 +220,44 @@ int check_generate(const mickey_streams *s, uint64_t n_bits, const void *out, in
   return check_limit(s, n_bits);
 }
 
+// Whether a launch of `bits` clocks should use the persistent kernel: only
+// when there are at least as many warp-groups as warps (one per SM
+// sub-partition) and the grid launch would leave a large part of its last
+// wave empty (a lone warp per sub-partition runs at ~95 % of the rate of
+// two, so below that the grid launch wins).
+bool use_persistent(const mickey_streams *s, int mode) {
+  const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * 4;
+  if (mode == MICKEY_MODE_GRID || W < slots) return false;
+  if (mode == MICKEY_MODE_PERSISTENT) return true;
+  const double waves = double((s->G + kKsThreads - 1) / kKsThreads) / (2.0 * s->sm_count);
+  const double eff = waves / std::ceil(waves);
+  return eff < 0.93;
+}
+
 // One keystream launch of `bits` clocks into a device buffer.
 int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
   KeystreamArgs ka{s->d_state, s->G, s->Gpad, s->n, bits, out};
-  CUDA_TRY(launch_keystream(ka, layout, s->unroll, s->stream), "keystream_kernel launch");
+  const auto &c = s->cfg[layout];
+  const int mode = c.set ? c.mode : s->mode;
+  const int unroll = c.set ? c.unroll : s->unroll;
+  const bool stage = c.set ? c.stage : s->stage;
+  if (use_persistent(s, mode)) {
+    const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * 4;
+    const uint64_t NT = (bits + 31) / 32;
+    PersistArgs pa;
+    pa.blocks = uint32_t(s->persist_blocks);
+    pa.W = uint32_t(W);
+    pa.L = (W * NT + slots - 1) / slots;
+    pa.flags = s->d_flags;
+    pa.epoch = ++s->epoch;
+    pa.spin_limit = 1u << 24;
+    pa.err = s->d_err;
+    CUDA_TRY(launch_keystream(ka, layout, unroll, stage, &pa, s->stream),
+             "keystream_persistent_kernel launch");
+  } else {
+    CUDA_TRY(launch_keystream(ka, layout, unroll, stage, nullptr, s->stream),
+             "keystream_kernel launch");
+  }
   return MICKEY_OK;
 }
 
@@ -419,6 +487,107 @@ mickey_streams *mickey_import_state(const uint8_t *states, const uint64_t *posit
   }
   ok();
   return s;
+}
+
+int mickey_set_config(mickey_streams *s, int layout, int mode, int unroll, int stage) {
+  if (!s) return fail(MICKEY_E_ARG, "handle must not be NULL");
+  if (!layout_ok(layout)) return fail(MICKEY_E_LAYOUT, "unknown layout %d", layout);
+  if (mode < MICKEY_MODE_AUTO || mode > MICKEY_MODE_PERSISTENT)
+    return fail(MICKEY_E_ARG, "unknown mode %d", mode);
+  bool known = false;
+  for (int k : kUnrolls) known |= (k == unroll);
+  if (!known) return fail(MICKEY_E_ARG, "unroll %d is not compiled (2 or 4)", unroll);
+  auto &c = s->cfg[layout];
+  c.set = true;
+  c.mode = mode;
+  c.unroll = unroll;
+  c.stage = stage != 0;
+  return ok();
+}
+
+int mickey_get_config(const mickey_streams *s, int layout, int *mode, int *unroll, int *stage) {
+  if (!s || !mode || !unroll || !stage) return fail(MICKEY_E_ARG, "NULL argument");
+  if (!layout_ok(layout)) return fail(MICKEY_E_LAYOUT, "unknown layout %d", layout);
+  const auto &c = s->cfg[layout];
+  *mode = c.set ? c.mode : s->mode;
+  *unroll = c.set ? c.unroll : s->unroll;
+  *stage = (c.set ? c.stage : s->stage) ? 1 : 0;
+  return ok();
+}
+
+int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout, mickey_tune_result *results,
+                int max_results, int *n_results) {
+  if (!s || n_bits == 0) return fail(MICKEY_E_ARG, "handle must not be NULL, n_bits > 0");
+  if (!layout_ok(layout)) return fail(MICKEY_E_LAYOUT, "unknown layout %d", layout);
+  if ((layout == MICKEY_LAYOUT_U32 || layout == MICKEY_LAYOUT_U32_F32) && n_bits % 32)
+    return fail(MICKEY_E_LAYOUT, "u32 layouts need n_bits %% 32 == 0");
+  int rc = MICKEY_OK;
+  if (n_bits > kMaxBitsPerCall) return fail(MICKEY_E_ARG, "n_bits per call is limited to 2^34");
+  const size_t out_sz = out_bytes(s->n, n_bits, layout);
+  const size_t st_sz = size_t(kStateRows) * s->Gpad * 4;
+  void *out = nullptr, *saved = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (out) cudaFree(out);
+    if (saved) cudaFree(saved);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&out, out_sz) != cudaSuccess || cudaMalloc(&saved, st_sz) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    return fail(MICKEY_E_OOM, "tuning buffers (%zu + %zu bytes)", out_sz, st_sz);
+  }
+  cudaMemcpyAsync(saved, s->d_state, st_sz, cudaMemcpyDeviceToDevice, s->stream);
+  const auto keep = s->cfg[layout];
+  const bool row = layout != MICKEY_LAYOUT_BITSLICED_U32;
+  const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * 4;
+  int count = 0;
+  float best_ms = 1e30f;
+  mickey_streams::LayoutCfg best = keep;
+  for (int mode : {MICKEY_MODE_GRID, MICKEY_MODE_PERSISTENT}) {
+    if (mode == MICKEY_MODE_PERSISTENT && W < slots) continue;
+    for (int unroll : kUnrolls) {
+      for (int stage = 0; stage <= (row && n_bits % 128 == 0 ? 1 : 0); ++stage) {
+        auto &c = s->cfg[layout];
+        c.set = true;
+        c.mode = mode;
+        c.unroll = unroll;
+        c.stage = stage != 0;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && rc == MICKEY_OK; ++rep) {
+          cudaMemcpyAsync(s->d_state, saved, st_sz, cudaMemcpyDeviceToDevice, s->stream);
+          cudaEventRecord(e0, s->stream);
+          rc = launch_generate(s, n_bits, out, layout);
+          cudaEventRecord(e1, s->stream);
+          if (rc == MICKEY_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = t < ms ? t : ms;
+          }
+        }
+        if (rc != MICKEY_OK) break;
+        if (results && count < max_results) results[count] = {mode, unroll, stage, ms};
+        ++count;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    }
+  }
+  cudaMemcpyAsync(s->d_state, saved, st_sz, cudaMemcpyDeviceToDevice, s->stream);
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  cleanup();
+  if (rc != MICKEY_OK) {
+    s->cfg[layout] = keep;
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tune sync");
+  s->cfg[layout] = best;
+  s->cfg[layout].set = true;
+  if (n_results) *n_results = count;
+  return ok();
 }
 
 void mickey_free(mickey_streams *s) { release(s); }

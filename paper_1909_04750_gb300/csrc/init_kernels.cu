@@ -70,10 +70,13 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
     }
     len[l] = v;
   }
+  // The IV phase runs a multiple of 4 clocks (the preclock loop handles four
+  // clocks per iteration); lanes are right-aligned to that length.
+  const int phase = (max_len + 3) & ~3;
 #pragma unroll
   for (int l = 0; l < 32; ++l)
-    if (l >= nv) len[l] = max_len;  // padding lanes: zero inputs, no masking
-  const bool mixed = min_len != max_len;
+    if (l >= nv) len[l] = phase;  // padding lanes: zero inputs, no masking
+  const bool mixed = min_len != phase;
 
   // Key bits: three 32-bit chunks per lane (the third holds bits 64..79).
 #pragma unroll 1
@@ -98,16 +101,16 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
   }
 
   // IV bits, right-aligned: lane l's bit b is consumed at IV clock
-  // b + (max_len - len[l]); before that the lane is inactive.
+  // b + (phase - len[l]); before that the lane is inactive (zero state).
 #pragma unroll 1
   for (int q = 0; q < 3; ++q) {
-    if (32 * q >= max_len) break;
+    if (32 * q >= phase) break;
     uint32_t m[32], act[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int l = 31 - r;
       const int L = len[l];
-      const int sft = max_len - L;
+      const int sft = phase - L;
       uint32_t w = 0;
       if (l < nv && L > 0) {
         const uint8_t *p = a.ivs + (base + l) * 10;
@@ -118,23 +121,28 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
         w = shift96_word(w0, w1, w2, sft, q);
       }
       m[r] = w;
-      act[r] = prefix_mask(max_len, q) & ~prefix_mask(sft, q);
+      act[r] = prefix_mask(phase, q) & ~prefix_mask(sft, q);
     }
     transpose32(m);
     if (mixed) transpose32(act);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int c = 32 * q + j;
-      if (c < max_len) {
+      if (c < phase) {
         a.scratch[size_t(kIvRow + c) * a.Gpad + g] = m[j];
         if (mixed) a.scratch[size_t(kActRow + c) * a.Gpad + g] = act[j];
       }
     }
   }
   a.scratch[size_t(kScratchRows) * a.Gpad + g] =
-      uint32_t(max_len) | (mixed ? 0x100u : 0u);
+      uint32_t(phase) | (mixed ? 0x100u : 0u);
 }
 
+constexpr int kPre = 2;  // clocks per loop iteration (IV phase is a multiple of 4)
+
+// kPre clocks per loop iteration: with a single clock per iteration the
+// shift of both registers makes every loop-carried word change register,
+// which costs copies and spills.
 __global__ void __launch_bounds__(kInitThreads) preclock_kernel(PreclockArgs a) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.G) return;
@@ -143,24 +151,35 @@ __global__ void __launch_bounds__(kInitThreads) preclock_kernel(PreclockArgs a) 
   for (int i = 0; i < kReg; ++i) r[i] = s[i] = 0u;
 
   const uint32_t info = a.scratch[size_t(kScratchRows) * a.Gpad + g];
-  const int max_len = int(info & 0xFFu);
+  const int phase = int(info & 0xFFu);  // IV clocks, a multiple of 4
   const bool mixed = (info >> 8) & 1u;
   const uint32_t *col = a.scratch + g;
   const size_t P = a.Gpad;
 
   if (mixed) {
 #pragma unroll 1
-    for (int c = 0; c < max_len; ++c)
-      clock_kg<true, true>(r, s, col[(kIvRow + c) * P], col[(kActRow + c) * P]);
+    for (int c = 0; c < phase; c += kPre) {
+#pragma unroll
+      for (int u = 0; u < kPre; ++u)
+        clock_kg<true, true>(r, s, col[(kIvRow + c + u) * P], col[(kActRow + c + u) * P]);
+    }
   } else {
 #pragma unroll 1
-    for (int c = 0; c < max_len; ++c)
-      clock_kg<true, false>(r, s, col[(kIvRow + c) * P], 0u);
+    for (int c = 0; c < phase; c += kPre) {
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) clock_kg<true, false>(r, s, col[(kIvRow + c + u) * P], 0u);
+    }
   }
 #pragma unroll 1
-  for (int j = 0; j < 80; ++j) clock_kg<true, false>(r, s, col[(kKeyRow + j) * P], 0u);
+  for (int j = 0; j < 80; j += kPre) {
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) clock_kg<true, false>(r, s, col[(kKeyRow + j + u) * P], 0u);
+  }
 #pragma unroll 1
-  for (int c = 0; c < 100; ++c) clock_kg<true, false>(r, s, 0u, 0u);
+  for (int c = 0; c < 100; c += kPre) {
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) clock_kg<true, false>(r, s, 0u, 0u);
+  }
 
   uint32_t *st = a.state + g;
 #pragma unroll

@@ -62,7 +62,22 @@ constexpr int kUnrolls[] = {2, 4};
 constexpr uint64_t kMaxBitsPerCall = 1ull << 34;
 constexpr int kKsThreads = 128;
 
-cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll,
-                             cudaStream_t st);
+// Persistent mode (see keystream_persistent_kernel): W warp-groups, L tiles
+// per warp, one flag word per warp-group (compared with `epoch`).
+struct PersistArgs {
+  uint32_t blocks;      // cooperative grid: one block of kKsThreads per SM
+  uint32_t W;           // warp-groups = ceil(G / 32)
+  uint64_t L;           // tiles of the work line per warp
+  uint32_t *flags;      // W words
+  uint32_t epoch;       // value a finished head piece writes
+  uint32_t spin_limit;  // bounded wait of a tail piece (iterations of ~256 ns)
+  int *err;
+};
+
+// p == nullptr: grid mode (one thread per group); else persistent mode.
+// stage: row layouts stage four tiles per row and write 16-byte chunks
+// (used when n_bits % 128 == 0 and `out` is 16-byte aligned).
+cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll, bool stage,
+                             const PersistArgs *p, cudaStream_t st);
 
 }  // namespace mickey

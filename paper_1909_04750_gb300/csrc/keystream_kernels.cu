@@ -22,7 +22,14 @@ struct EmitCtx {
   uint32_t lane_mask;  // valid lanes of this group (last group may be partial)
   bool vec_ok;         // 16-byte vector stores allowed (bitsliced layout)
   bool word_ok;        // 4-byte row stores allowed (bytes layout)
+  bool stage;          // row layouts: stage 4 tiles per row, 16-byte stores
 };
+
+// Shared memory of a keystream block: two tile buffers (32 words per
+// thread each) and, when rows are staged, 4 words per row per thread laid
+// out [row][thread][4] so that a thread's 16-byte reads are conflict-free.
+constexpr size_t kTileBufWords = 2 * 32 * kKsThreads;
+constexpr size_t kRowStageWords = 32 * kKsThreads * 4;
 
 template <int J>
 __device__ __forceinline__ void swap_bits(uint32_t &lo, uint32_t &hi) {
@@ -39,15 +46,20 @@ __device__ __forceinline__ void swap_halves(uint32_t &lo, uint32_t &hi) {
   lo = a;
 }
 // Block swap of size 8 (bytes 1 and 3 of hi into bytes 0 and 2 of lo and
-// bytes 0 and 2 of lo into bytes 1 and 3 of hi).
+// bytes 0 and 2 of lo into bytes 1 and 3 of hi).  With BSWAP the two results
+// come out byte-reversed (the selectors read in the opposite byte order),
+// which turns a big-endian word into its memory byte order for free.
+template <bool BSWAP>
 __device__ __forceinline__ void swap_bytes(uint32_t &lo, uint32_t &hi) {
-  const uint32_t a = __byte_perm(lo, hi, 0x3715);
-  hi = __byte_perm(lo, hi, 0x2604);
+  const uint32_t a = __byte_perm(lo, hi, BSWAP ? 0x5173 : 0x3715);
+  hi = __byte_perm(lo, hi, BSWAP ? 0x4062 : 0x2604);
   lo = a;
 }
 
-// Store lane l's 32 keystream bits t0..t0+nb-1 (z_{t0} in bit 31).  `tile`
-// points at row 32g, column t0 of the output; rows are `pitch` bytes apart.
+// Store lane l's 32 keystream bits t0..t0+nb-1.  `word` holds z_{t0} in bit
+// 31, except for the bytes layout, where it arrives byte-reversed (z_{t0} in
+// bit 7, i.e. in memory byte order).  `tile` points at row 32g, column t0 of
+// the output; rows are `pitch` bytes apart.
 template <int LAYOUT>
 __device__ __forceinline__ void store_row_word(uint8_t *tile, uint32_t pitch,
                                                uint64_t f32_off, int l, int nb,
@@ -55,10 +67,10 @@ __device__ __forceinline__ void store_row_word(uint8_t *tile, uint32_t pitch,
   uint8_t *o = tile + uint64_t(uint32_t(l) * pitch);
   if constexpr (LAYOUT == MICKEY_LAYOUT_BYTES) {
     if (nb == 32 && e.word_ok) {
-      *reinterpret_cast<uint32_t *>(o) = __byte_perm(word, 0u, 0x0123);
+      *reinterpret_cast<uint32_t *>(o) = word;
     } else {
       const int nbytes = (nb + 7) >> 3;
-      for (int b = 0; b < nbytes; ++b) o[b] = uint8_t(word >> (24 - 8 * b));
+      for (int b = 0; b < nbytes; ++b) o[b] = uint8_t(word >> (8 * b));
     }
   } else {
     *reinterpret_cast<uint32_t *>(o) = word;
@@ -67,77 +79,127 @@ __device__ __forceinline__ void store_row_word(uint8_t *tile, uint32_t pitch,
   }
 }
 
+// One eighth of the emission of a 32-clock tile held in shared memory
+// (column `z`, stride kKsThreads).  Slices must run in order 0..7:
+//   bitsliced  slice j stores words 4j..4j+3 (one 128-bit store);
+//   row-major  slices 0-3 apply the block swaps of size 4, 2, 1 to rows
+//              8j..8j+7 in place; slices 4-7 apply the swaps of size 16 and 8
+//              to rows {k, k+8, k+16, k+24} for k = 2(j-4), 2(j-4)+1 and
+//              store the finished words.  The five swaps commute, so the
+//              result is transpose32() of the tile.
 template <int LAYOUT>
-__device__ __forceinline__ void emit_tile(const uint32_t *zcol,
-                                          const KeystreamArgs &a, uint32_t g,
-                                          uint64_t t0, int nb,
-                                          const EmitCtx &e) {
+__device__ __forceinline__ void emit_slice(uint32_t *z, uint32_t *rb, const KeystreamArgs &a,
+                                           uint32_t g, uint64_t t0, int nb,
+                                           const EmitCtx &e, int j) {
   if constexpr (LAYOUT == MICKEY_LAYOUT_BITSLICED_U32) {
     uint32_t *o = static_cast<uint32_t *>(a.out) + size_t(g) * a.n_bits + t0;
     if (nb == 32 && e.vec_ok) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        uint4 v;
-        v.x = zcol[(4 * q + 0) * kKsThreads] & e.lane_mask;
-        v.y = zcol[(4 * q + 1) * kKsThreads] & e.lane_mask;
-        v.z = zcol[(4 * q + 2) * kKsThreads] & e.lane_mask;
-        v.w = zcol[(4 * q + 3) * kKsThreads] & e.lane_mask;
-        reinterpret_cast<uint4 *>(o)[q] = v;
-      }
+      uint4 v;
+      v.x = z[(4 * j + 0) * kKsThreads] & e.lane_mask;
+      v.y = z[(4 * j + 1) * kKsThreads] & e.lane_mask;
+      v.z = z[(4 * j + 2) * kKsThreads] & e.lane_mask;
+      v.w = z[(4 * j + 3) * kKsThreads] & e.lane_mask;
+      reinterpret_cast<uint4 *>(o)[j] = v;
     } else {
-      for (int c = 0; c < nb; ++c) o[c] = zcol[c * kKsThreads] & e.lane_mask;
+      for (int c = 4 * j; c < 4 * j + 4 && c < nb; ++c) o[c] = z[c * kKsThreads] & e.lane_mask;
     }
+  } else if (j < 4) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = z[(8 * j + k) * kKsThreads];
+    swap_bits<4>(v[0], v[4]); swap_bits<4>(v[1], v[5]);
+    swap_bits<4>(v[2], v[6]); swap_bits<4>(v[3], v[7]);
+    swap_bits<2>(v[0], v[2]); swap_bits<2>(v[1], v[3]);
+    swap_bits<2>(v[4], v[6]); swap_bits<2>(v[5], v[7]);
+    swap_bits<1>(v[0], v[1]); swap_bits<1>(v[2], v[3]);
+    swap_bits<1>(v[4], v[5]); swap_bits<1>(v[6], v[7]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) z[(8 * j + k) * kKsThreads] = v[k];
   } else {
-    // Un-bitslice the 32x32 tile in two passes over shared memory, eight or
-    // four words live at a time: the block swaps of size 4, 2, 1 act within
-    // 8-row chunks and those of size 16, 8 within the rows {k, k+8, k+16,
-    // k+24}; the five swaps commute, so this equals transpose32().
-    uint32_t *z = const_cast<uint32_t *>(zcol);
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-      uint32_t v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = z[(8 * c + k) * kKsThreads];
-      swap_bits<4>(v[0], v[4]); swap_bits<4>(v[1], v[5]);
-      swap_bits<4>(v[2], v[6]); swap_bits<4>(v[3], v[7]);
-      swap_bits<2>(v[0], v[2]); swap_bits<2>(v[1], v[3]);
-      swap_bits<2>(v[4], v[6]); swap_bits<2>(v[5], v[7]);
-      swap_bits<1>(v[0], v[1]); swap_bits<1>(v[2], v[3]);
-      swap_bits<1>(v[4], v[5]); swap_bits<1>(v[6], v[7]);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) z[(8 * c + k) * kKsThreads] = v[k];
-    }
     const uint32_t pitch = LAYOUT == MICKEY_LAYOUT_BYTES ? uint32_t((a.n_bits + 7) >> 3)
                                                          : uint32_t(a.n_bits >> 3);
     uint8_t *tile = static_cast<uint8_t *>(a.out) + 32ull * g * pitch + (t0 >> 3);
     const uint64_t f32_off = uint64_t(pitch) * a.n;  // float block follows
-#pragma unroll 1
-    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * (j - 4) + h;
       uint32_t v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) v[q] = z[(k + 8 * q) * kKsThreads];
       swap_halves(v[0], v[2]);
       swap_halves(v[1], v[3]);
-      swap_bytes(v[0], v[1]);
-      swap_bytes(v[2], v[3]);
+      swap_bytes<LAYOUT == MICKEY_LAYOUT_BYTES>(v[0], v[1]);
+      swap_bytes<LAYOUT == MICKEY_LAYOUT_BYTES>(v[2], v[3]);
       // row k + 8q of the transposed tile is lane 31 - k - 8q
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int l = 31 - k - 8 * q;
-        if ((e.lane_mask >> l) & 1u) store_row_word<LAYOUT>(tile, pitch, f32_off, l, nb, e, v[q]);
+        if (e.stage && nb == 32)
+          rb[l * (kKsThreads * 4) + ((t0 >> 5) & 3)] = v[q];
+        else if ((e.lane_mask >> l) & 1u)
+          store_row_word<LAYOUT>(tile, pitch, f32_off, l, nb, e, v[q]);
       }
     }
   }
 }
 
-template <int LAYOUT, int U>
-__global__ void __launch_bounds__(kKsThreads)
-    keystream_kernel(KeystreamArgs a, EmitCtx e) {
-  __shared__ uint32_t zs[32 * kKsThreads];
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.G) return;
-  const size_t P = a.Gpad;
+template <int LAYOUT>
+__device__ __forceinline__ void emit_tile(uint32_t *z, uint32_t *rb, const KeystreamArgs &a,
+                                          uint32_t g, uint64_t t0, int nb, const EmitCtx &e) {
+#pragma unroll 1
+  for (int j = 0; j < 8; ++j) emit_slice<LAYOUT>(z, rb, a, g, t0, nb, e, j);
+}
 
+// Row layouts with staging: write the staged words of tiles tA..tB (one
+// aligned block of four tiles, or part of one) of every valid row; a whole
+// block goes out as one 16-byte store per row (and per f32 row).
+template <int LAYOUT>
+__device__ __forceinline__ void flush_rows(const uint32_t *rb, const KeystreamArgs &a,
+                                           uint32_t g, uint32_t tA, uint32_t tB,
+                                           const EmitCtx &e) {
+  const uint32_t pitch = uint32_t(a.n_bits >> 3);
+  uint8_t *base = static_cast<uint8_t *>(a.out) + 32ull * g * pitch + uint64_t(tA) * 4;
+  const uint64_t f32_off = uint64_t(pitch) * a.n;
+  const int n = int(tB - tA) + 1, j0 = int(tA & 3);
+#pragma unroll 1
+  for (int l = 0; l < 32; ++l) {
+    if (!((e.lane_mask >> l) & 1u)) continue;
+    const uint32_t *src = rb + l * (kKsThreads * 4);
+    uint8_t *o = base + uint64_t(uint32_t(l) * pitch);
+    if (n == 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(src);
+      *reinterpret_cast<uint4 *>(o) = v;
+      if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32) {
+        float4 f;
+        f.x = __uint2float_rn(v.x >> 8) * 0x1p-24f;
+        f.y = __uint2float_rn(v.y >> 8) * 0x1p-24f;
+        f.z = __uint2float_rn(v.z >> 8) * 0x1p-24f;
+        f.w = __uint2float_rn(v.w >> 8) * 0x1p-24f;
+        *reinterpret_cast<float4 *>(o + f32_off) = f;
+      }
+    } else {
+      for (int j = 0; j < n; ++j) {
+        const uint32_t w = src[j0 + j];
+        reinterpret_cast<uint32_t *>(o)[j] = w;
+        if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32)
+          reinterpret_cast<float *>(o + f32_off)[j] = __uint2float_rn(w >> 8) * 0x1p-24f;
+      }
+    }
+  }
+}
+
+// Keystream bits of tiles [tile_a, tile_b) of group g (tile t covers clocks
+// 32t .. 32t+31 of this call; the last tile may be partial), continuing from
+// and writing back the group's state.  The tile buffer is double-buffered:
+// while the 32 clocks of tile k run (U clocks per step), the eight emission
+// slices of tile k-1 are interleaved with them, so the clock's independent
+// LOP3s hide the latency of the emission's shared-memory and global accesses.
+template <int LAYOUT, int U>
+__device__ __forceinline__ void run_piece(const KeystreamArgs &a, EmitCtx e, uint32_t g,
+                                          uint32_t *zbuf0, uint32_t *zbuf1, uint32_t *rb,
+                                          uint32_t tile_a, uint32_t tile_b) {
+  static_assert(U == 2 || U == 4, "one emission slice per 4 clocks");
+  const size_t P = a.Gpad;
   uint32_t r[kReg], s[kReg];
   const uint32_t *src = a.state + g;
 #pragma unroll
@@ -147,33 +209,43 @@ __global__ void __launch_bounds__(kKsThreads)
   }
   if (g != a.G - 1) e.lane_mask = ~0u;
 
-  uint32_t *zcol = zs + threadIdx.x;
-  const uint64_t full_end = a.n_bits & ~uint64_t(31);
-  uint64_t t0 = 0;
+  const uint32_t full = uint32_t(a.n_bits >> 5);
+  const uint32_t fend = tile_b < full ? tile_b : full;
 #pragma unroll 1
-  for (; t0 < full_end; t0 += 32) {
+  for (uint32_t tile = tile_a; tile < fend; ++tile) {
+    uint32_t *cur = (tile & 1) ? zbuf1 : zbuf0;
+    uint32_t *prev = (tile & 1) ? zbuf0 : zbuf1;
 #pragma unroll 1
     for (int c = 0; c < 32; c += U) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        zcol[(c + u) * kKsThreads] = r[0] ^ s[0];
+        cur[(c + u) * kKsThreads] = r[0] ^ s[0];
         clock_kg<false, false>(r, s, 0u, 0u);
       }
+      if (tile > tile_a && (c & 3) == 0)
+        emit_slice<LAYOUT>(prev, rb, a, g, uint64_t(tile - 1) << 5, 32, e, c >> 2);
     }
-    emit_tile<LAYOUT>(zcol, a, g, t0, 32, e);
+    if (LAYOUT != MICKEY_LAYOUT_BITSLICED_U32 && e.stage && tile > tile_a && ((tile - 1) & 3) == 3)
+      flush_rows<LAYOUT>(rb, a, g, max(tile - 4, tile_a), tile - 1, e);
   }
-  if (t0 < a.n_bits) {
-    const int rem = int(a.n_bits - t0);
+  if (fend > tile_a) {
+    emit_tile<LAYOUT>((fend & 1) ? zbuf0 : zbuf1, rb, a, g, uint64_t(fend - 1) << 5, 32, e);
+    if (LAYOUT != MICKEY_LAYOUT_BITSLICED_U32 && e.stage)
+      flush_rows<LAYOUT>(rb, a, g, max((fend - 1) & ~3u, tile_a), fend - 1, e);
+  }
+  if (tile_b > full && (a.n_bits & 31)) {  // the partial last tile
+    uint32_t *cur = (full & 1) ? zbuf1 : zbuf0;
+    const int rem = int(a.n_bits & 31);
 #pragma unroll 1
     for (int c = 0; c < 32; ++c) {
       if (c < rem) {
-        zcol[c * kKsThreads] = r[0] ^ s[0];
+        cur[c * kKsThreads] = r[0] ^ s[0];
         clock_kg<false, false>(r, s, 0u, 0u);
       } else {
-        zcol[c * kKsThreads] = 0u;
+        cur[c * kKsThreads] = 0u;
       }
     }
-    emit_tile<LAYOUT>(zcol, a, g, t0, rem, e);
+    emit_tile<LAYOUT>(cur, rb, a, g, uint64_t(full) << 5, rem, e);
   }
 
   uint32_t *dst = a.state + g;
@@ -184,37 +256,189 @@ __global__ void __launch_bounds__(kKsThreads)
   }
 }
 
+// Grid mode: one thread per group, all tiles.
+template <int LAYOUT, int U>
+__global__ void __launch_bounds__(kKsThreads)
+    keystream_kernel(KeystreamArgs a, EmitCtx e) {
+  extern __shared__ uint32_t zs[];
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.G) return;
+  run_piece<LAYOUT, U>(a, e, g, zs + threadIdx.x, zs + 32 * kKsThreads + threadIdx.x,
+                       zs + kTileBufWords + 4 * threadIdx.x, 0,
+                       uint32_t((a.n_bits + 31) >> 5));
+}
+
+__device__ __forceinline__ uint32_t load_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void store_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Persistent mode: one warp per SM sub-partition, launched cooperatively
+// (all warps resident).  The work line -- warp-group w (32 groups) x tile t,
+// W x NT tiles in all -- is cut into equal segments, one per warp, so every
+// sub-partition gets the same work even when W is not a multiple of the
+// warp count.  A segment holds at most one piece of the warp-group it
+// starts in (a tail: tiles ta..NT) and one of the group it ends in (a head:
+// tiles 0..tb).  A warp runs its head piece first and publishes the state,
+// then its whole groups, then its tail piece, which continues from the
+// state the previous segment's head published (bounded acquire-spin; on
+// timeout the error flag is raised and the piece is skipped).
+// Piece k (in processing order) of the work-line segment of warp `slot`:
+// warp-group w, tiles [ta, tb).  Returns false past the last piece.  The
+// order is: the head of the last warp-group (if the segment ends inside it),
+// the whole warp-groups, the tail of the first warp-group (if the segment
+// starts inside it).  Recomputed per piece so that only (slot, k) stay live
+// across the clock loop.
+__device__ __forceinline__ bool segment_piece(const PersistArgs &p, uint64_t NT, uint32_t slot,
+                                              uint32_t k, uint32_t &w, uint32_t &ta,
+                                              uint32_t &tb) {
+  const uint64_t total = uint64_t(p.W) * NT;
+  const uint64_t seg_a = uint64_t(slot) * p.L;
+  const uint64_t seg_b = seg_a + p.L < total ? seg_a + p.L : total;
+  if (seg_a >= seg_b) return false;
+  const uint64_t w_first = seg_a / NT, w_last = (seg_b - 1) / NT;
+  const bool has_tail = seg_a > w_first * NT;
+  const bool has_head = (seg_b - w_last * NT) < NT && !(has_tail && w_last == w_first);
+  const uint64_t full_lo = w_first + (has_tail ? 1 : 0);
+  const uint64_t full_end = w_last + 1 - (has_head ? 1 : 0);
+  const uint64_t full_n = full_end > full_lo ? full_end - full_lo : 0;
+  const uint64_t n_pieces = (has_head ? 1 : 0) + full_n + (has_tail ? 1 : 0);
+  if (k >= n_pieces) return false;
+  const uint64_t kk = k - (has_head ? 1 : 0);
+  const uint64_t ww = (has_head && k == 0) ? w_last : (kk < full_n ? full_lo + kk : w_first);
+  w = uint32_t(ww);
+  ta = uint32_t(ww == w_first ? seg_a - ww * NT : 0);
+  tb = uint32_t(ww == w_last ? seg_b - ww * NT : NT);
+  return true;
+}
+
+// Persistent mode: one warp per SM sub-partition, launched cooperatively
+// (all warps resident).  The work line -- warp-group w (32 groups) x tile t,
+// W x NT tiles in all -- is cut into equal segments, one per warp, so every
+// sub-partition gets the same work even when W is not a multiple of the
+// warp count.  A segment holds at most one piece of the warp-group it
+// starts in (a tail: tiles ta..NT) and one of the group it ends in (a head:
+// tiles 0..tb).  A warp runs its head piece first and publishes the state,
+// then its whole groups, then its tail piece, which continues from the
+// state the previous segment's head published (bounded acquire-spin; on
+// timeout the error flag is raised and the piece is skipped).
+template <int LAYOUT, int U>
+__global__ void __launch_bounds__(kKsThreads, 1)
+    keystream_persistent_kernel(KeystreamArgs a, EmitCtx e, PersistArgs p) {
+  extern __shared__ uint32_t zs[];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t slot = blockIdx.x * (kKsThreads / 32) + (threadIdx.x >> 5);
+  const uint64_t NT = (a.n_bits + 31) >> 5;
+#pragma unroll 1
+  for (uint32_t k = 0;; ++k) {
+    uint32_t w, ta, tb;
+    if (!segment_piece(p, NT, slot, k, w, ta, tb)) break;
+    if (ta > 0) {  // tail: wait for the head piece of this warp-group
+      uint32_t it = 0;
+      bool ok = true;
+      while (load_acquire(p.flags + w) != p.epoch) {
+        if (++it > p.spin_limit) {
+          ok = false;
+          break;
+        }
+        __nanosleep(256);
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(p.err, kErrTimeout);
+        continue;
+      }
+    }
+    const uint32_t g = w * 32 + lane;
+    if (g < a.G)
+      run_piece<LAYOUT, U>(a, e, g, zs + threadIdx.x, zs + 32 * kKsThreads + threadIdx.x,
+                           zs + kTileBufWords + 4 * threadIdx.x, ta, tb);
+    if (ta == 0 && tb < NT) {  // head: publish the state for the next segment
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) store_release(p.flags + w, p.epoch);
+    }
+  }
+}
+
+size_t smem_bytes(const EmitCtx &e) {
+  return 4 * (kTileBufWords + (e.stage ? kRowStageWords : 0));
+}
+
+template <class K>
+cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(4 * (kTileBufWords + kRowStageWords)));
+}
+
+template <int LAYOUT, int U>
+cudaError_t launch_persistent(const KeystreamArgs &a, const EmitCtx &e, const PersistArgs &p,
+                              cudaStream_t st) {
+  cudaError_t err = allow_smem(keystream_persistent_kernel<LAYOUT, U>);
+  if (err != cudaSuccess) return err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.dynamicSmemBytes = smem_bytes(e);
+  cfg.gridDim = dim3(p.blocks);
+  cfg.blockDim = dim3(kKsThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, keystream_persistent_kernel<LAYOUT, U>, a, e, p);
+}
+
 template <int LAYOUT>
 cudaError_t launch_layout(const KeystreamArgs &a, int unroll, const EmitCtx &e,
-                          cudaStream_t st) {
+                          const PersistArgs *p, cudaStream_t st) {
+  if (p) {
+    cudaError_t err = unroll == 2 ? launch_persistent<LAYOUT, 2>(a, e, *p, st)
+                      : unroll == 4 ? launch_persistent<LAYOUT, 4>(a, e, *p, st)
+                                    : cudaErrorInvalidValue;
+    return err != cudaSuccess ? err : cudaGetLastError();
+  }
   const uint32_t blocks = (a.G + kKsThreads - 1) / kKsThreads;
+  const size_t smem = smem_bytes(e);
+  cudaError_t err = cudaSuccess;
   switch (unroll) {
-    case 2: keystream_kernel<LAYOUT, 2><<<blocks, kKsThreads, 0, st>>>(a, e); break;
-    case 4: keystream_kernel<LAYOUT, 4><<<blocks, kKsThreads, 0, st>>>(a, e); break;
+    case 2:
+      err = allow_smem(keystream_kernel<LAYOUT, 2>);
+      if (err == cudaSuccess) keystream_kernel<LAYOUT, 2><<<blocks, kKsThreads, smem, st>>>(a, e);
+      break;
+    case 4:
+      err = allow_smem(keystream_kernel<LAYOUT, 4>);
+      if (err == cudaSuccess) keystream_kernel<LAYOUT, 4><<<blocks, kKsThreads, smem, st>>>(a, e);
+      break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll,
-                             cudaStream_t st) {
+cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll, bool stage,
+                             const PersistArgs *p, cudaStream_t st) {
   EmitCtx e;
   const uint32_t tail = uint32_t(a.n & 31u);
   e.lane_mask = tail ? ((1u << tail) - 1u) : ~0u;
-  const uintptr_t p = reinterpret_cast<uintptr_t>(a.out);
-  e.vec_ok = (p % 16 == 0) && (a.n_bits % 4 == 0);
-  e.word_ok = (p % 4 == 0) && (((a.n_bits + 7) / 8) % 4 == 0);
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(a.out);
+  e.vec_ok = (addr % 16 == 0) && (a.n_bits % 4 == 0);
+  e.word_ok = (addr % 4 == 0) && (((a.n_bits + 7) / 8) % 4 == 0);
+  e.stage = stage && layout != MICKEY_LAYOUT_BITSLICED_U32 && (addr % 16 == 0) &&
+            (a.n_bits % 128 == 0);
   switch (layout) {
     case MICKEY_LAYOUT_BITSLICED_U32:
-      return launch_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, unroll, e, st);
+      return launch_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, unroll, e, p, st);
     case MICKEY_LAYOUT_BYTES:
-      return launch_layout<MICKEY_LAYOUT_BYTES>(a, unroll, e, st);
+      return launch_layout<MICKEY_LAYOUT_BYTES>(a, unroll, e, p, st);
     case MICKEY_LAYOUT_U32:
-      return launch_layout<MICKEY_LAYOUT_U32>(a, unroll, e, st);
+      return launch_layout<MICKEY_LAYOUT_U32>(a, unroll, e, p, st);
     case MICKEY_LAYOUT_U32_F32:
-      return launch_layout<MICKEY_LAYOUT_U32_F32>(a, unroll, e, st);
+      return launch_layout<MICKEY_LAYOUT_U32_F32>(a, unroll, e, p, st);
     default:
       return cudaErrorInvalidValue;
   }

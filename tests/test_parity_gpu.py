@@ -268,3 +268,59 @@ def test_fused_full_size_sampled():
     assert _first_diff(got, ref) is None
     del both, u, f, chk
     torch.cuda.empty_cache()
+
+
+# -------------------------------------------------------------- persistent mode
+
+@pytest.mark.parametrize("stage", ["0", "1"])
+@pytest.mark.parametrize("n,n_bits,blocks", [(10 * 1024, 1000, 1), (7 * 1024 + 5, 4096, 1),
+                                             (41 * 1024 - 3, 776, 2), (20 * 1024, 64, 3),
+                                             (10 * 1024, 4096, 3), (41 * 1024 - 3, 1024, 2)])
+def test_persistent_mode_matches_grid_and_oracle(monkeypatch, n, n_bits, blocks, stage):
+    # The work line is cut into 4*blocks equal segments, so warp-groups are
+    # split into head and tail pieces run by different warps.
+    s = workloads.plain_scale(n)
+    monkeypatch.setenv("MICKEY_STAGE", stage)
+    monkeypatch.setenv("MICKEY_MODE", "grid")
+    st_g = _streams(s)
+    monkeypatch.setenv("MICKEY_MODE", "persistent")
+    monkeypatch.setenv("MICKEY_PERSIST_BLOCKS", str(blocks))
+    st_p = _streams(s)
+    got = {}
+    for layout in ("bytes", "bitsliced", "u32_f32"):
+        if layout == "u32_f32" and n_bits % 32:
+            continue
+        a = st_g.generate(n_bits, layout).cpu().numpy()
+        b = st_p.generate(n_bits, layout).cpu().numpy()
+        st_p.sync()
+        assert np.array_equal(a, b), layout
+        got[layout] = b
+    # the second call continued every stream: check sampled rows bit-exactly
+    rows = _sample_rows(n, 64, 5)
+    ref = _ref(s.subset(rows), 3 * n_bits)
+    bits = oracle.bits_of(ref, 3 * n_bits)[:, n_bits:2 * n_bits]
+    bs = got["bitsliced"]
+    for k, r in enumerate(rows):
+        lane = ((bs[r // 32].view(np.uint32) >> np.uint32(r % 32)) & 1).astype(np.uint8)
+        assert np.array_equal(lane, bits[k]), int(r)
+    assert np.array_equal(got["bytes"][rows], ref[:, : (n_bits + 7) // 8]) or n_bits % 8
+    if "u32_f32" in got:
+        u = oracle.to_u32(ref[:, 2 * n_bits // 8:], n_bits)
+        assert np.array_equal(got["u32_f32"][0][rows].view(np.uint32), u)
+        assert np.array_equal(got["u32_f32"][1][rows].view(np.float32), oracle.to_f32(u))
+
+
+def test_autotune_keeps_positions_and_output():
+    from paper_1909_04750_gb300 import autotune
+    s = workloads.plain_scale(24 * 1024)
+    st = _streams(s)
+    first = st.generate(256, "bytes").cpu().numpy()
+    entry = autotune.tune(st, 1024, N.LAYOUT_BYTES, refresh=True)
+    assert entry["candidates"] and entry["unroll"] in (2, 4)
+    assert st.position(0) == 256          # tuning restored the state
+    rest = st.generate(1024, "bytes").cpu().numpy()
+    st.sync()
+    rows = _sample_rows(s.n, 64, 3)
+    ref = _ref(s.subset(rows), 1280)
+    assert np.array_equal(first[rows], ref[:, :32])
+    assert np.array_equal(rest[rows], ref[:, 32:])
