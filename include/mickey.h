@@ -196,6 +196,37 @@ MICKEY_API int mickey_get_config(const mickey_streams *s, int layout, int *mode,
 MICKEY_API int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout,
                            mickey_tune_result *results, int max_results, int *n_results);
 
+/* --------------------------------------------------------------------------
+ * Allocation-free key/IV loading.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory -- code
+ * running inside an application whose own allocator owns the GPU's memory,
+ * or a latency-bound loop that must not pay for a new allocation or for the
+ * device synchronisation cudaFree implies.  It runs the same loading and
+ * preclocking as mickey_init_streams, but its temporary memory is a fixed
+ * array inside the library (about 3.6 MB, held on every GPU that loads the
+ * library until the process exits), so it calls no allocator.
+ *
+ *  keys, ivs   host memory, n x 10 bytes; iv_lens host memory, n values
+ *              (NULL = 80 bits each); all copied into the fixed array.
+ *  n           1 .. MICKEY_NOALLOC_MAX_STREAMS.
+ *  state       caller-owned DEVICE buffer of 200 * P words with
+ *              P = 32 * ceil(ceil(n / 32) / 32): word w of group g at
+ *              state[w * P + g] (w = 0..99: r0..r99, 100..199: s0..s99),
+ *              bit l = instance 32g + l.
+ *  cuda_stream the work is enqueued there; the call returns at once.
+ *  Returns MICKEY_OK, MICKEY_E_ARG (NULL pointer, n == 0, n above the
+ *  maximum), MICKEY_E_IVLEN, MICKEY_E_CUDA; it does not set
+ *  mickey_last_error.
+ *  The first call on a device looks up the array's device address
+ *  (cudaGetSymbolAddress), so make that call before any stream capture.
+ *  Every call uses the same array and leaves its contents behind: calls
+ *  whose work overlaps on the GPU race and must be serialised.
+ * ------------------------------------------------------------------------ */
+#define MICKEY_NOALLOC_MAX_STREAMS 65536
+MICKEY_API int mickey_init_state_noalloc(const uint8_t *keys, const uint8_t *ivs,
+                                         const uint32_t *iv_lens, size_t n, uint32_t *state,
+                                         void *cuda_stream);
+
 /* Synchronise, release all device memory of the handle.  NULL is a no-op. */
 MICKEY_API void mickey_free(mickey_streams *s);
 

@@ -58,6 +58,8 @@ SIGNATURES = {
     "mickey_set_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "mickey_get_config": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "mickey_tune": (c_int, [c_void_p, c_uint64, c_int, c_void_p, c_int, c_void_p]),
+    "mickey_init_state_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p,
+                                          c_void_p]),
 }
 
 
