@@ -1,0 +1,39 @@
+"""Run one workload shape through the library, for profilers.
+
+    python -m paper_1909_04750_gb300.profile_case --n 1048576 --n-bits 2048 --layout bytes
+
+Creates a handle for ``workloads.plain_scale(n)`` (device inputs), then
+``--reps`` times re-keys it and generates ``n_bits`` per stream in
+``layout``.  The launch configuration comes from the environment
+(MICKEY_MODE, MICKEY_UNROLL, MICKEY_STAGE) or the library defaults.
+"""
+import argparse
+
+import torch
+
+from . import workloads
+from .build import build
+from .streams import Streams
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--n", type=int, default=1 << 20)
+    p.add_argument("--n-bits", type=int, default=2048)
+    p.add_argument("--layout", default="bytes")
+    p.add_argument("--reps", type=int, default=2)
+    a = p.parse_args()
+    build()
+    s = workloads.plain_scale(a.n)
+    k, v = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
+    st = Streams(k, v)
+    for _ in range(a.reps):
+        st.reset(k, v)
+        st.generate(a.n_bits, a.layout)
+    st.sync()
+    torch.cuda.synchronize()
+    print("ok", vars(a))
+
+
+if __name__ == "__main__":
+    main()
