@@ -197,6 +197,55 @@ MICKEY_API int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout,
                            mickey_tune_result *results, int max_results, int *n_results);
 
 /* --------------------------------------------------------------------------
+ * Batched generation: n streams, each with its own keystream length and IV
+ * length, generated in one persistent launch (loading, preclocks and
+ * keystream captured once as a CUDA graph, replayed by every run).  Streams
+ * are packed into 32-lane groups longest first; warps take 32 groups at a
+ * time from an atomic work queue in that order (longest processing time
+ * first).  Output: stream i's keystream as row-major bytes (layout 1) of
+ * ceil(n_bits[i] / 8) bytes at byte offset offsets[i] of `out`, offsets in
+ * the caller's order, each 16-byte aligned; bytes between rows are not
+ * written.
+ * ------------------------------------------------------------------------ */
+typedef struct mickey_batch mickey_batch;
+
+/* Plan a batch for host arrays iv_lens (NULL = 80 each) and n_bits
+ * (0 .. 2^40 each); allocates the device buffers and captures the graph on
+ * the stream's device.  NULL on error (mickey_last_error: MICKEY_E_ARG,
+ * MICKEY_E_IVLEN, MICKEY_E_LIMIT, MICKEY_E_OOM, MICKEY_E_CUDA). */
+MICKEY_API mickey_batch *mickey_batch_create(const uint32_t *iv_lens, const uint64_t *n_bits,
+                                             size_t n, void *cuda_stream);
+/* Total bytes the output buffer must hold. */
+MICKEY_API size_t mickey_batch_output_bytes(const mickey_batch *b);
+/* Byte offset of each stream's keystream in the output (n values). */
+MICKEY_API int mickey_batch_offsets(const mickey_batch *b, uint64_t *offsets);
+/* Clocks of the longest group (a lower bound on the run's critical path)
+ * and the sum over groups (the work); either pointer may be NULL. */
+MICKEY_API int mickey_batch_clocks(const mickey_batch *b, uint64_t *max_clocks,
+                                   uint64_t *total_clocks);
+/* Generate every stream of the batch: keys and ivs (n x 10 bytes each, in
+ * `mem`: MICKEY_MEM_HOST or MICKEY_MEM_DEVICE) are copied in, then the graph
+ * is launched on the batch's stream; `out` is a device buffer of
+ * mickey_batch_output_bytes bytes.  Asynchronous. */
+MICKEY_API int mickey_batch_run(mickey_batch *b, const void *keys, const void *ivs, void *out,
+                                int mem);
+/* Launch configuration of the batch's keystream kernel: clocks per inner
+ * step (2 or 4), resident blocks of 4 warps per SM (1 or 2), and
+ * split_clocks: groups needing more clocks than this are each run by a whole
+ * warp (lane j clocks register bits 4j..4j+3, about ten times less time per
+ * clock, for long streams whose sequential clocks bound the run); 0 disables
+ * the split path.  Re-captures the graph. */
+MICKEY_API int mickey_batch_set_config(mickey_batch *b, int unroll, int blocks_per_sm,
+                                       uint64_t split_clocks);
+/* split_clocks / split_groups may be NULL. */
+MICKEY_API int mickey_batch_get_config(const mickey_batch *b, int *unroll, int *blocks_per_sm,
+                                       uint64_t *split_clocks, uint32_t *split_groups);
+/* Wait for the batch's stream; MICKEY_E_IVLEN if the device saw a bad IV
+ * length. */
+MICKEY_API int mickey_batch_sync(mickey_batch *b);
+MICKEY_API void mickey_batch_free(mickey_batch *b);
+
+/* --------------------------------------------------------------------------
  * Allocation-free key/IV loading.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory -- code
  * running inside an application whose own allocator owns the GPU's memory,

@@ -58,6 +58,15 @@ SIGNATURES = {
     "mickey_set_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "mickey_get_config": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "mickey_tune": (c_int, [c_void_p, c_uint64, c_int, c_void_p, c_int, c_void_p]),
+    "mickey_batch_create": (c_void_p, [c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mickey_batch_output_bytes": (c_size_t, [c_void_p]),
+    "mickey_batch_offsets": (c_int, [c_void_p, c_void_p]),
+    "mickey_batch_clocks": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "mickey_batch_run": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "mickey_batch_set_config": (c_int, [c_void_p, c_int, c_int, c_uint64]),
+    "mickey_batch_get_config": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "mickey_batch_sync": (c_int, [c_void_p]),
+    "mickey_batch_free": (None, [c_void_p]),
     "mickey_init_state_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p,
                                           c_void_p]),
 }

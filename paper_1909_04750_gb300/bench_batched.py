@@ -1,0 +1,81 @@
+"""Benchmark of the batched workload: 100,000 streams, keystream lengths
+log-uniform in [2^10, 2^22] bits, IV lengths in {0, 16, ..., 80}, seed 3, in
+one persistent launch replayed from a CUDA graph.
+
+    python -m paper_1909_04750_gb300.bench_batched [--runs K] [--n N]
+
+Prints one JSON line: Gbit/s over all streams, and the two lower bounds on a
+run's time -- the work at the plain kernel's measured rate, and the critical
+path (the longest group's clocks at the measured time per clock of a group
+running alone; MICKEY has no jump-ahead, so a stream's bits are produced one
+clock after another).
+"""
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import workloads
+from .batch import Batch, tune
+from .build import build
+from .streams import Streams
+
+
+def lone_group_ns_per_clock(n_bits: int = 1 << 16) -> float:
+    """Time per clock of one 32-lane group alone on the GPU."""
+    s = workloads.plain_scale(32)
+    st = Streams(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
+    out = st.generate(n_bits, "bitsliced")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st.generate(n_bits, "bitsliced", out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    st.free()
+    return e0.elapsed_time(e1) * 1e6 / n_bits
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--runs", type=int, default=3)
+    p.add_argument("--n", type=int, default=workloads.BATCHED["n"])
+    p.add_argument("--plain-gbit-s", type=float, default=None,
+                   help="plain-workload throughput for the work bound (measured if absent)")
+    a = p.parse_args()
+    build()
+    s = workloads.batched(a.n)
+    keys, ivs = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
+    b = Batch(s.n_bits, s.iv_lens)
+    out = torch.empty(b.output_bytes, dtype=torch.uint8, device="cuda")
+    tuned = tune(b, keys, ivs, out)
+    b.run(keys, ivs, out)
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(a.runs):
+        e0.record(b.stream)
+        b.run(keys, ivs, out)
+        e1.record(b.stream)
+        b.sync()
+        times.append(e0.elapsed_time(e1))
+    ms = min(times)
+    bits = int(s.n_bits.sum())
+    t_clk = lone_group_ns_per_clock()
+    crit_ms = b.max_clocks * t_clk * 1e-6
+    line = {
+        "metric": "batched keystream Gbit/s (100k ragged streams, one persistent launch)",
+        "value": bits / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms_per_run": ms,
+        "runs": a.runs, "streams": b.n, "keystream_bits": bits,
+        "groups_clocks_total": b.total_clocks, "longest_group_clocks": b.max_clocks,
+        "lone_group_ns_per_clock": t_clk, "critical_path_ms": crit_ms,
+        "config": {"unroll": tuned["unroll"], "blocks_per_sm": tuned["blocks_per_sm"]},
+    }
+    if a.plain_gbit_s:
+        line["work_bound_ms"] = bits / (a.plain_gbit_s * 1e9) * 1e3
+    print(json.dumps(line), flush=True)
+    b.free()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,558 @@
+// Batched generation: many streams of uneven keystream length and IV
+// length in one persistent launch.
+//
+// Plan (host, once per shape): streams are sorted by keystream length,
+// longest first, and packed 32 at a time into bitsliced groups, so the
+// lanes of a group need similar numbers of clocks; a group runs as many
+// clocks as its longest lane and each lane keeps only its own bits.  Each
+// stream's output is its own row-major byte string at a 16-byte aligned
+// offset (in the caller's stream order).
+//
+// Run (device, captured once as a CUDA graph and replayed): key/IV loading
+// through the sorting permutation, preclock, then one persistent keystream
+// kernel whose warps take work items -- 32 consecutive groups, i.e. one group
+// per thread -- from an atomic counter.  Items are numbered longest first,
+// so the longest groups start first (longest-processing-time order) and the
+// short ones fill in behind them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/mickey.h"
+#include "bitslice.cuh"
+#include "internal.h"
+
+using namespace mickey;
+
+namespace {
+
+constexpr int kBatchThreads = 128;
+
+struct BatchParams {  // device-side, written before each graph launch
+  uint8_t *out;
+};
+
+struct BatchArgs {
+  const uint32_t *state;     // kStateRows x Gpad, group order
+  uint32_t G, Gpad;
+  const uint64_t *slot_off;  // 32*Gpad: byte offset of the slot's stream in out
+  const uint64_t *slot_bits; // 32*Gpad: keystream bits of the slot's stream (0: padding)
+  const uint64_t *group_bits;// Gpad: clocks of the group (its longest lane)
+  uint32_t n_split;          // groups 0..n_split-1 run on a whole warp each
+  uint32_t n_items;          // n_split + ceil((G - n_split) / 32)
+  uint32_t *queue;           // item counter, zero at launch
+  const BatchParams *params;
+};
+
+// Store word w (memory byte order) of the lane's tile t, clipped to the
+// lane's n_bits (bits past the end of a last partial byte are zeroed).
+__device__ __forceinline__ void store_ragged(uint8_t *out, const BatchArgs &a, uint64_t slot,
+                                             uint32_t t, uint32_t w) {
+  const uint64_t bits = __ldg(a.slot_bits + slot);
+  const uint64_t b0 = uint64_t(t) << 5;
+  if (b0 >= bits) return;
+  uint8_t *o = out + __ldg(a.slot_off + slot) + (b0 >> 3);
+  const uint64_t left = bits - b0;
+  if (left >= 32) {
+    *reinterpret_cast<uint32_t *>(o) = w;
+    return;
+  }
+  const uint32_t keep_be = ~0u << (32 - uint32_t(left));            // big-endian bit order
+  w &= __byte_perm(keep_be, 0u, 0x0123);                               // to memory order
+  const int nbytes = int((left + 7) >> 3);
+  for (int b = 0; b < nbytes; ++b) o[b] = uint8_t(w >> (8 * b));
+}
+
+// One eighth of the emission of tile t (see the keystream kernels: slices
+// 0-3 swap blocks of size 4, 2, 1 in place, slices 4-7 swap blocks of size
+// 16, 8 and store), for ragged rows.
+__device__ __forceinline__ void batch_slice(uint32_t *z, uint8_t *out, const BatchArgs &a,
+                                            uint32_t g, uint32_t t, int j) {
+  if (j < 4) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = z[(8 * j + k) * kBatchThreads];
+    swap_bits<4>(v[0], v[4]); swap_bits<4>(v[1], v[5]);
+    swap_bits<4>(v[2], v[6]); swap_bits<4>(v[3], v[7]);
+    swap_bits<2>(v[0], v[2]); swap_bits<2>(v[1], v[3]);
+    swap_bits<2>(v[4], v[6]); swap_bits<2>(v[5], v[7]);
+    swap_bits<1>(v[0], v[1]); swap_bits<1>(v[2], v[3]);
+    swap_bits<1>(v[4], v[5]); swap_bits<1>(v[6], v[7]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) z[(8 * j + k) * kBatchThreads] = v[k];
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * (j - 4) + h;
+      uint32_t v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = z[(k + 8 * q) * kBatchThreads];
+      swap_halves(v[0], v[2]);
+      swap_halves(v[1], v[3]);
+      swap_bytes<true>(v[0], v[1]);
+      swap_bytes<true>(v[2], v[3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        store_ragged(out, a, uint64_t(g) * 32 + (31 - k - 8 * q), t, v[q]);
+    }
+  }
+}
+
+template <int U>
+__device__ __forceinline__ void batch_group(const BatchArgs &a, uint8_t *out, uint32_t g,
+                                            uint32_t *zb0, uint32_t *zb1) {
+  const size_t P = a.Gpad;
+  uint32_t r[kReg], s[kReg];
+  const uint32_t *src = a.state + g;
+#pragma unroll
+  for (int i = 0; i < kReg; ++i) {
+    r[i] = src[size_t(i) * P];
+    s[i] = src[size_t(kReg + i) * P];
+  }
+  const uint64_t clocks = a.group_bits[g];
+  const uint32_t full = uint32_t(clocks >> 5);
+#pragma unroll 1
+  for (uint32_t tile = 0; tile < full; ++tile) {
+    uint32_t *cur = (tile & 1) ? zb1 : zb0;
+    uint32_t *prev = (tile & 1) ? zb0 : zb1;
+#pragma unroll 1
+    for (int c = 0; c < 32; c += U) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        cur[(c + u) * kBatchThreads] = r[0] ^ s[0];
+        clock_kg<false, false>(r, s, 0u, 0u);
+      }
+      if (tile > 0 && (c & 3) == 0) batch_slice(prev, out, a, g, tile - 1, c >> 2);
+    }
+  }
+  if (full > 0) {
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) batch_slice((full & 1) ? zb0 : zb1, out, a, g, full - 1, j);
+  }
+  const int rem = int(clocks & 31);
+  if (rem) {
+    uint32_t *cur = (full & 1) ? zb1 : zb0;
+#pragma unroll 1
+    for (int c = 0; c < 32; ++c) {
+      if (c < rem) {
+        cur[c * kBatchThreads] = r[0] ^ s[0];
+        clock_kg<false, false>(r, s, 0u, 0u);
+      } else {
+        cur[c * kBatchThreads] = 0u;
+      }
+    }
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) batch_slice(cur, out, a, g, full, j);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split path for long groups: one warp clocks one group, so a clock costs
+// about 34 logic ops per lane instead of ~390 per thread.  Lane j (< 25) owns
+// register bits 4j .. 4j+3 of R and of S (slots 0..3); lanes 25..31 carry
+// no bits.  Each clock the warp exchanges neighbour words (r_{4j-1},
+// s_{4j-1}, s_{4j+4}) and broadcasts the control and feedback words (s34,
+// r67, s67, r33, r99, s99) with shuffles; the table constants become per-lane
+// masks.  The keystream word z = r0 ^ s0 (lane 0) is broadcast each clock
+// and kept by lane c for clock c; every 32 clocks 32 ballots give each lane
+// its instance's 32 bits.
+
+struct SplitMasks {
+  uint32_t rtap[4], comp0[4], comp1[4], fb0[4], fb1[4];
+};
+constexpr SplitMasks make_split_masks() {
+  SplitMasks m{};
+  for (int i = 0; i < kReg; ++i) {
+    const uint32_t b = 1u << (i % 32);
+    if (rtap(i)) m.rtap[i / 32] |= b;
+    if (comp0(i)) m.comp0[i / 32] |= b;
+    if (comp1(i)) m.comp1[i / 32] |= b;
+    if (fb0(i)) m.fb0[i / 32] |= b;
+    if (fb1(i)) m.fb1[i / 32] |= b;
+  }
+  return m;
+}
+__constant__ SplitMasks kSplitMasks = make_split_masks();
+
+__device__ __forceinline__ uint32_t bit_mask(const uint32_t (&w)[4], int i) {
+  return (i < kReg && ((w[i >> 5] >> (i & 31)) & 1u)) ? ~0u : 0u;
+}
+
+struct SplitLane {
+  uint32_t tap[4], c0[4], c1[4], en[4], fb0[4], fb1[4];
+};
+
+__device__ __forceinline__ void split_lane_masks(uint32_t lane, SplitLane &k) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = int(4 * lane) + q;
+    k.tap[q] = bit_mask(kSplitMasks.rtap, i);
+    k.c0[q] = bit_mask(kSplitMasks.comp0, i);
+    k.c1[q] = bit_mask(kSplitMasks.comp1, i);
+    k.fb0[q] = bit_mask(kSplitMasks.fb0, i);
+    k.fb1[q] = bit_mask(kSplitMasks.fb1, i);
+    // non-linear term of s^_i exists for i = 1..98 only
+    k.en[q] = (i >= 1 && i <= 98) ? ~0u : 0u;
+  }
+}
+
+// One non-mixing CLOCK_KG of the group spread over the warp.
+__device__ __forceinline__ void clock_split(uint32_t (&r)[4], uint32_t (&s)[4], const SplitLane &k,
+                                            uint32_t lane) {
+  constexpr uint32_t F = 0xffffffffu;
+  const uint32_t up_ok = lane ? ~0u : 0u;
+  const uint32_t r_up = __shfl_up_sync(F, r[3], 1) & up_ok;   // r_{4j-1} (r_{-1} = 0)
+  const uint32_t s_up = __shfl_up_sync(F, s[3], 1) & up_ok;   // s_{4j-1}
+  const uint32_t s_dn = __shfl_down_sync(F, s[0], 1);         // s_{4j+4}
+  const uint32_t cbr = __shfl_sync(F, s[2], 8) ^ __shfl_sync(F, r[3], 16);   // s34 ^ r67
+  const uint32_t cbs = __shfl_sync(F, s[3], 16) ^ __shfl_sync(F, r[1], 8);   // s67 ^ r33
+  const uint32_t fbr = __shfl_sync(F, r[3], 24);                              // r99
+  const uint32_t fbs = __shfl_sync(F, s[3], 24);                              // s99
+  const uint32_t f0 = fbs & ~cbs, f1 = fbs & cbs;
+  uint32_t nr[4], ns[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t rm1 = q ? r[q - 1] : r_up;
+    nr[q] = rm1 ^ (cbr & r[q]) ^ (fbr & k.tap[q]);
+    const uint32_t sm1 = q ? s[q - 1] : s_up;
+    const uint32_t sp1 = q < 3 ? s[q + 1] : s_dn;
+    // bits 0 and 99 (no non-linear term) sit in slots 0 and 3 only; the
+    // dummy lanes' results never reach a real bit
+    const uint32_t a = (q == 0 || q == 3) ? ((s[q] ^ k.c0[q]) & k.en[q]) : (s[q] ^ k.c0[q]);
+    const uint32_t nl = a & (sp1 ^ k.c1[q]);
+    ns[q] = sm1 ^ nl ^ (f0 & k.fb0[q]) ^ (f1 & k.fb1[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    r[q] = nr[q];
+    s[q] = ns[q];
+  }
+}
+
+// Emit a 32-clock tile: lane c holds the keystream word of clock c (zt);
+// 32 ballots give lane l its instance's bits, clock c in bit c, which are
+// reversed (z of the tile's first clock first) and put in memory byte order.
+__device__ __forceinline__ void split_emit(uint32_t zt, uint8_t *out, const BatchArgs &a,
+                                           uint32_t g, uint32_t lane, uint32_t t) {
+  uint32_t mine = 0;
+#pragma unroll
+  for (int l = 0; l < 32; ++l) {
+    const uint32_t w = __ballot_sync(0xffffffffu, (zt >> l) & 1u);
+    mine = lane == uint32_t(l) ? w : mine;
+  }
+  store_ragged(out, a, uint64_t(g) * 32 + lane, t, __byte_perm(__brev(mine), 0u, 0x0123));
+}
+
+// One clock plus keeping z = r0 ^ s0 (lane 0's slot 0) of clock c in lane c.
+__device__ __forceinline__ void split_step(uint32_t (&r)[4], uint32_t (&s)[4], const SplitLane &k,
+                                           uint32_t lane, int c, uint32_t &zt) {
+  const uint32_t z = __shfl_sync(0xffffffffu, r[0] ^ s[0], 0);
+  zt = lane == uint32_t(c) ? z : zt;
+  clock_split(r, s, k, lane);
+}
+
+__device__ __forceinline__ void split_group(const BatchArgs &a, uint8_t *out, uint32_t g,
+                                            uint32_t lane) {
+  SplitLane k;
+  split_lane_masks(lane, k);
+  const size_t P = a.Gpad;
+  uint32_t r[4], s[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = int(4 * lane) + q;
+    r[q] = i < kReg ? a.state[size_t(i) * P + g] : 0u;
+    s[q] = i < kReg ? a.state[size_t(kReg + i) * P + g] : 0u;
+  }
+  const uint64_t clocks = a.group_bits[g];
+  const uint32_t full = uint32_t(clocks >> 5);
+#pragma unroll 1
+  for (uint32_t t = 0; t < full; ++t) {
+    uint32_t zt = 0;
+#pragma unroll 1
+    for (int c = 0; c < 32; c += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) split_step(r, s, k, lane, c + u, zt);
+    }
+    split_emit(zt, out, a, g, lane, t);
+  }
+  const int rem = int(clocks & 31);
+  if (rem) {
+    uint32_t zt = 0;
+#pragma unroll 1
+    for (int c = 0; c < rem; ++c) split_step(r, s, k, lane, c, zt);
+    split_emit(zt, out, a, g, lane, full);
+  }
+}
+
+// Work items in queue order: first one item per split group (groups
+// 0 .. n_split-1, the longest), each run by a whole warp; then items of 32
+// consecutive groups, one per thread.
+template <int U>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
+  __shared__ uint32_t zs[2 * 32 * kBatchThreads];
+  const uint32_t lane = threadIdx.x & 31u;
+  uint8_t *out = a.params->out;
+#pragma unroll 1
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(a.queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= a.n_items) break;
+    if (item < a.n_split) {
+      split_group(a, out, item, lane);
+      continue;
+    }
+    const uint32_t g = a.n_split + (item - a.n_split) * 32 + lane;
+    if (g < a.G)
+      batch_group<U>(a, out, g, zs + threadIdx.x, zs + 32 * kBatchThreads + threadIdx.x);
+  }
+}
+
+bool valid_unroll(int u) { return u == 2 || u == 4; }
+
+}  // namespace
+
+struct mickey_batch {
+  size_t n = 0;
+  uint32_t G = 0, Gpad = 0;
+  uint64_t out_bytes = 0, max_clocks = 0, total_clocks = 0;
+  std::vector<uint64_t> offsets;  // per stream, caller order
+  std::vector<uint64_t> group_clocks;  // longest first
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int unroll = 4, blocks_per_sm = 2;
+  uint64_t split_clocks = 0;      // groups longer than this use the split path (0: none)
+  uint32_t n_split = 0;
+  // device
+  uint8_t *d_in = nullptr;        // keys (10n), ivs (10n), iv_lens (4n) in caller order
+  uint32_t *d_perm = nullptr;     // 32*Gpad
+  uint64_t *d_slot = nullptr;     // slot_off (32*Gpad), slot_bits (32*Gpad), group_bits (Gpad)
+  uint32_t *d_state = nullptr, *d_scratch = nullptr, *d_queue = nullptr;
+  int *d_err = nullptr;
+  BatchParams *d_params = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batch_release(mickey_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_in);
+  cudaFree(b->d_perm);
+  cudaFree(b->d_slot);
+  cudaFree(b->d_state);
+  cudaFree(b->d_scratch);
+  cudaFree(b->d_queue);
+  cudaFree(b->d_err);
+  cudaFree(b->d_params);
+  delete b;
+}
+
+// Capture load + preclock + persistent keystream into a graph.
+cudaError_t capture(mickey_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const size_t n = b->n;
+    cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), cs);
+    LoadArgs la{b->d_in, b->d_in + 10 * n, reinterpret_cast<const uint32_t *>(b->d_in + 20 * n),
+                n, b->d_perm, b->G, b->Gpad, b->d_scratch, b->d_err};
+    launch_load(la, cs);
+    PreclockArgs pa{b->d_scratch, b->d_state, b->G, b->Gpad};
+    launch_preclock(pa, cs);
+    BatchArgs ba{b->d_state, b->G, b->Gpad, b->d_slot, b->d_slot + 32 * size_t(b->Gpad),
+                 b->d_slot + 64 * size_t(b->Gpad), b->n_split,
+                 b->n_split + (b->G - b->n_split + 31) / 32, b->d_queue, b->d_params};
+    const uint32_t grid = uint32_t(b->sm_count * b->blocks_per_sm);
+    if (b->unroll == 2)
+      batch_kernel<2><<<grid, kBatchThreads, 0, cs>>>(ba);
+    else
+      batch_kernel<4><<<grid, kBatchThreads, 0, cs>>>(ba);
+    e = cudaStreamEndCapture(cs, &b->graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  cudaStreamDestroy(cs);
+  return e;
+}
+
+int copy_inputs(mickey_batch *b, const void *keys, const void *ivs, int mem) {
+  const cudaMemcpyKind kind =
+      mem == MICKEY_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (cudaMemcpyAsync(b->d_in, keys, 10 * b->n, kind, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_in + 10 * b->n, ivs, 10 * b->n, kind, b->stream) != cudaSuccess)
+    return MICKEY_E_CUDA;
+  return MICKEY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+MICKEY_API mickey_batch *mickey_batch_create(const uint32_t *iv_lens, const uint64_t *n_bits,
+                                             size_t n, void *cuda_stream) {
+  if (!n_bits || n == 0 || n > (size_t(1) << 31)) {
+    set_error(MICKEY_E_ARG, "n_bits must not be NULL and 0 < n <= 2^31");
+    return nullptr;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    if (n_bits[i] > MICKEY_MAX_STREAM_BITS) {
+      set_error(MICKEY_E_LIMIT, "a stream asks for more than 2^40 keystream bits");
+      return nullptr;
+    }
+    if (iv_lens && iv_lens[i] > MICKEY_MAX_IV_BITS) {
+      set_error(MICKEY_E_IVLEN, "an IV length exceeds 80 bits");
+      return nullptr;
+    }
+  }
+  mickey_batch *b = new (std::nothrow) mickey_batch;
+  if (!b) {
+    set_error(MICKEY_E_OOM, "host allocation failed");
+    return nullptr;
+  }
+  b->n = n;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->G = uint32_t((n + 31) / 32);
+  b->Gpad = (b->G + 31u) & ~31u;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+
+  // longest first; ties keep the caller's order
+  std::vector<uint32_t> order(n);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t x, uint32_t y) { return n_bits[x] > n_bits[y]; });
+  b->offsets.resize(n);
+  uint64_t off = 0;
+  for (size_t i = 0; i < n; ++i) {  // caller order, 16-byte aligned rows
+    b->offsets[i] = off;
+    off += ((n_bits[i] + 7) / 8 + 15) & ~uint64_t(15);
+  }
+  b->out_bytes = off;
+  b->group_clocks.resize(b->G);
+  const size_t slots = 32 * size_t(b->Gpad);
+  std::vector<uint32_t> perm(slots, 0u);
+  std::vector<uint64_t> slot(2 * slots + b->Gpad, 0);
+  for (size_t j = 0; j < n; ++j) {
+    perm[j] = order[j];
+    slot[j] = b->offsets[order[j]];
+    slot[slots + j] = n_bits[order[j]];
+  }
+  for (uint32_t g = 0; g < b->G; ++g) {
+    const uint64_t c = n_bits[order[size_t(g) * 32]];  // longest lane of the group
+    slot[2 * slots + g] = c;
+    b->group_clocks[g] = c;
+    b->total_clocks += c;
+    b->max_clocks = std::max(b->max_clocks, c);
+  }
+  bool ok = cudaMalloc(&b->d_in, 24 * n) == cudaSuccess &&
+            cudaMalloc(&b->d_perm, slots * 4) == cudaSuccess &&
+            cudaMalloc(&b->d_slot, slot.size() * 8) == cudaSuccess &&
+            cudaMalloc(&b->d_state, size_t(kStateRows) * b->Gpad * 4) == cudaSuccess &&
+            cudaMalloc(&b->d_scratch, size_t(kScratchRows + 1) * b->Gpad * 4) == cudaSuccess &&
+            cudaMalloc(&b->d_queue, 4) == cudaSuccess &&
+            cudaMalloc(&b->d_err, 4) == cudaSuccess &&
+            cudaMalloc(&b->d_params, sizeof(BatchParams)) == cudaSuccess;
+  if (ok) {
+    std::vector<uint32_t> lens(n, 80u);
+    if (iv_lens) std::copy(iv_lens, iv_lens + n, lens.begin());
+    ok = cudaMemcpy(b->d_in + 20 * n, lens.data(), 4 * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_perm, perm.data(), slots * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_slot, slot.data(), slot.size() * 8, cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemset(b->d_err, 0, 4) == cudaSuccess && capture(b) == cudaSuccess;
+  }
+  if (!ok) {
+    batch_release(b);
+    set_error(MICKEY_E_CUDA, "device allocation, upload or graph capture failed");
+    return nullptr;
+  }
+  set_error(MICKEY_OK, "");
+  return b;
+}
+
+MICKEY_API size_t mickey_batch_output_bytes(const mickey_batch *b) {
+  return b ? size_t(b->out_bytes) : 0;
+}
+
+MICKEY_API int mickey_batch_offsets(const mickey_batch *b, uint64_t *offsets) {
+  if (!b || !offsets) return MICKEY_E_ARG;
+  std::memcpy(offsets, b->offsets.data(), b->n * 8);
+  return MICKEY_OK;
+}
+
+MICKEY_API int mickey_batch_clocks(const mickey_batch *b, uint64_t *max_clocks,
+                                   uint64_t *total_clocks) {
+  if (!b) return MICKEY_E_ARG;
+  if (max_clocks) *max_clocks = b->max_clocks;
+  if (total_clocks) *total_clocks = b->total_clocks;
+  return MICKEY_OK;
+}
+
+MICKEY_API int mickey_batch_run(mickey_batch *b, const void *keys, const void *ivs, void *out,
+                                int mem) {
+  if (!b || !keys || !ivs || !out) return MICKEY_E_ARG;
+  if (mem != MICKEY_MEM_HOST && mem != MICKEY_MEM_DEVICE) return MICKEY_E_ARG;
+  int rc = copy_inputs(b, keys, ivs, mem);
+  if (rc) return rc;
+  BatchParams p{static_cast<uint8_t *>(out)};
+  if (cudaMemcpyAsync(b->d_params, &p, sizeof p, cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
+      cudaGraphLaunch(b->exec, b->stream) != cudaSuccess)
+    return MICKEY_E_CUDA;
+  return MICKEY_OK;
+}
+
+MICKEY_API int mickey_batch_set_config(mickey_batch *b, int unroll, int blocks_per_sm,
+                                       uint64_t split_clocks) {
+  if (!b || !valid_unroll(unroll) || blocks_per_sm < 1 || blocks_per_sm > 2) return MICKEY_E_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MICKEY_E_CUDA;
+  b->unroll = unroll;
+  b->blocks_per_sm = blocks_per_sm;
+  b->split_clocks = split_clocks;
+  uint32_t ns = 0;
+  if (split_clocks)
+    while (ns < b->G && b->group_clocks[ns] > split_clocks) ++ns;
+  b->n_split = ns;
+  return capture(b) == cudaSuccess ? MICKEY_OK : MICKEY_E_CUDA;
+}
+
+MICKEY_API int mickey_batch_get_config(const mickey_batch *b, int *unroll, int *blocks_per_sm,
+                                       uint64_t *split_clocks, uint32_t *split_groups) {
+  if (!b || !unroll || !blocks_per_sm) return MICKEY_E_ARG;
+  *unroll = b->unroll;
+  *blocks_per_sm = b->blocks_per_sm;
+  if (split_clocks) *split_clocks = b->split_clocks;
+  if (split_groups) *split_groups = b->n_split;
+  return MICKEY_OK;
+}
+
+MICKEY_API int mickey_batch_sync(mickey_batch *b) {
+  if (!b) return MICKEY_E_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MICKEY_E_CUDA;
+  int flag = 0;
+  if (cudaMemcpy(&flag, b->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return MICKEY_E_CUDA;
+  if (flag) {
+    cudaMemset(b->d_err, 0, 4);
+    return (flag & kErrIvLen) ? MICKEY_E_IVLEN : MICKEY_E_TIMEOUT;
+  }
+  return MICKEY_OK;
+}
+
+MICKEY_API void mickey_batch_free(mickey_batch *b) { batch_release(b); }
+
+}  // extern "C"

@@ -111,4 +111,31 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
   stage(std::integral_constant<int, 1>{}, 0x55555555u);
 }
 
+// Block swaps of the two-pass 32x32 transpose used to un-bitslice a tile
+// (see the keystream kernels).
+template <int J>
+__device__ __forceinline__ void swap_bits(uint32_t &lo, uint32_t &hi) {
+  constexpr uint32_t m = J == 4 ? 0x0F0F0F0Fu : J == 2 ? 0x33333333u : 0x55555555u;
+  const uint32_t t = (lo ^ (hi >> J)) & m;
+  lo ^= t;
+  hi ^= t << J;
+}
+// Block swap of size 16: lo keeps its high half and takes hi's high half;
+// hi keeps its low half and takes lo's low half.
+__device__ __forceinline__ void swap_halves(uint32_t &lo, uint32_t &hi) {
+  const uint32_t a = __byte_perm(lo, hi, 0x3276);
+  hi = __byte_perm(lo, hi, 0x1054);
+  lo = a;
+}
+// Block swap of size 8 (bytes 1 and 3 of hi into bytes 0 and 2 of lo and
+// bytes 0 and 2 of lo into bytes 1 and 3 of hi).  With BSWAP the two results
+// come out byte-reversed (the selectors read in the opposite byte order),
+// which turns a big-endian word into its memory byte order for free.
+template <bool BSWAP>
+__device__ __forceinline__ void swap_bytes(uint32_t &lo, uint32_t &hi) {
+  const uint32_t a = __byte_perm(lo, hi, BSWAP ? 0x5173 : 0x3715);
+  hi = __byte_perm(lo, hi, BSWAP ? 0x4062 : 0x2604);
+  lo = a;
+}
+
 }  // namespace mickey

@@ -191,7 +191,7 @@ int run_init(mickey_streams *s, const void *keys, const void *ivs,
     di = static_cast<const uint8_t *>(ivs);
     dl = iv_lens;
   }
-  LoadArgs la{dk, di, dl, n, s->G, s->Gpad, s->d_scratch, s->d_err};
+  LoadArgs la{dk, di, dl, n, nullptr, s->G, s->Gpad, s->d_scratch, s->d_err};
   CUDA_TRY(launch_load(la, s->stream), "load_kernel launch");
   PreclockArgs pa{s->d_scratch, s->d_state, s->G, s->Gpad};
   CUDA_TRY(launch_preclock(pa, s->stream), "preclock_kernel launch");
@@ -262,6 +262,10 @@ int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
 }
 
 }  // namespace
+
+namespace mickey {
+int set_error(int code, const char *msg) { return code ? fail(code, "%s", msg) : ok(); }
+}  // namespace mickey
 
 extern "C" {
 

@@ -47,6 +47,11 @@ __device__ __forceinline__ uint32_t shift96_word(uint32_t w0, uint32_t w1,
   return __funnelshift_r(lo, hi, bs);
 }
 
+// Instance held by lane slot `slot` (32g + l).
+__device__ __forceinline__ uint64_t inst(const LoadArgs &a, uint64_t slot) {
+  return a.perm ? uint64_t(a.perm[slot]) : slot;
+}
+
 __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.G) return;
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
   for (int l = 0; l < 32; ++l) {
     int v = 0;
     if (l < nv) {
-      v = a.iv_lens ? int(min(a.iv_lens[base + l], 1000u)) : 80;
+      v = a.iv_lens ? int(min(a.iv_lens[inst(a, base + l)], 1000u)) : 80;
       if (v > 80) {
         atomicOr(a.err, kErrIvLen);
         v = 80;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
       const int l = 31 - r;  // row r = lane 31-r, so result bit l = lane l
       uint32_t w = 0;
       if (l < nv) {
-        const uint8_t *p = a.keys + (base + l) * 10 + 4 * q;
+        const uint8_t *p = a.keys + inst(a, base + l) * 10 + 4 * q;
         w = q < 2 ? load_be32(p) : (uint32_t(p[0]) << 24) | (uint32_t(p[1]) << 16);
       }
       m[r] = w;
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
       const int sft = phase - L;
       uint32_t w = 0;
       if (l < nv && L > 0) {
-        const uint8_t *p = a.ivs + (base + l) * 10;
+        const uint8_t *p = a.ivs + inst(a, base + l) * 10;
         const uint32_t w0 = load_be32(p) & prefix_mask(L, 0);
         const uint32_t w1 = load_be32(p + 4) & prefix_mask(L, 1);
         const uint32_t w2 =

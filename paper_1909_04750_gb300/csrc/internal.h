@@ -33,6 +33,7 @@ struct LoadArgs {
   const uint8_t *ivs;       // n x 10, device
   const uint32_t *iv_lens;  // n, device, or nullptr (= 80)
   uint64_t n;
+  const uint32_t *perm;     // lane slot -> instance, or nullptr (identity)
   uint32_t G, Gpad;
   uint32_t *scratch;        // kScratchRows * Gpad + Gpad words
   int *err;
@@ -54,6 +55,10 @@ struct KeystreamArgs {
   uint64_t n_bits;          // keystream bits per instance in this call
   void *out;                // device output, layout-dependent
 };
+
+// Record the thread-local error reported by mickey_last_error (code 0
+// clears it); returns `code`.
+int set_error(int code, const char *msg);
 
 // Unroll factors compiled for the keystream kernel.
 constexpr int kUnrolls[] = {2, 4};

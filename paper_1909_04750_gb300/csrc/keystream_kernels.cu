@@ -26,35 +26,13 @@ struct EmitCtx {
 };
 
 // Shared memory of a keystream block: two tile buffers (32 words per
-// thread each) and, when rows are staged, 4 words per row per thread laid
-// out [row][thread][4] so that a thread's 16-byte reads are conflict-free.
+// thread each) and, when rows are staged, ST words per row per thread laid
+// out [row][thread][ST].  The grid kernel (two blocks per SM) stages ST = 4
+// tiles (16-byte row stores); the persistent kernel (one block per SM)
+// stages ST = 8 tiles, i.e. whole 32-byte sectors, so that no partially
+// written sector has to be merged in L2 or re-read from DRAM.
 constexpr size_t kTileBufWords = 2 * 32 * kKsThreads;
-constexpr size_t kRowStageWords = 32 * kKsThreads * 4;
-
-template <int J>
-__device__ __forceinline__ void swap_bits(uint32_t &lo, uint32_t &hi) {
-  constexpr uint32_t m = J == 4 ? 0x0F0F0F0Fu : J == 2 ? 0x33333333u : 0x55555555u;
-  const uint32_t t = (lo ^ (hi >> J)) & m;
-  lo ^= t;
-  hi ^= t << J;
-}
-// Block swap of size 16: lo keeps its high half and takes hi's high half;
-// hi keeps its low half and takes lo's low half.
-__device__ __forceinline__ void swap_halves(uint32_t &lo, uint32_t &hi) {
-  const uint32_t a = __byte_perm(lo, hi, 0x3276);
-  hi = __byte_perm(lo, hi, 0x1054);
-  lo = a;
-}
-// Block swap of size 8 (bytes 1 and 3 of hi into bytes 0 and 2 of lo and
-// bytes 0 and 2 of lo into bytes 1 and 3 of hi).  With BSWAP the two results
-// come out byte-reversed (the selectors read in the opposite byte order),
-// which turns a big-endian word into its memory byte order for free.
-template <bool BSWAP>
-__device__ __forceinline__ void swap_bytes(uint32_t &lo, uint32_t &hi) {
-  const uint32_t a = __byte_perm(lo, hi, BSWAP ? 0x5173 : 0x3715);
-  hi = __byte_perm(lo, hi, BSWAP ? 0x4062 : 0x2604);
-  lo = a;
-}
+constexpr size_t row_stage_words(int st) { return size_t(32) * kKsThreads * st; }
 
 // Store lane l's 32 keystream bits t0..t0+nb-1.  `word` holds z_{t0} in bit
 // 31, except for the bytes layout, where it arrives byte-reversed (z_{t0} in
@@ -87,7 +65,7 @@ __device__ __forceinline__ void store_row_word(uint8_t *tile, uint32_t pitch,
 //              to rows {k, k+8, k+16, k+24} for k = 2(j-4), 2(j-4)+1 and
 //              store the finished words.  The five swaps commute, so the
 //              result is transpose32() of the tile.
-template <int LAYOUT>
+template <int LAYOUT, int ST>
 __device__ __forceinline__ void emit_slice(uint32_t *z, uint32_t *rb, const KeystreamArgs &a,
                                            uint32_t g, uint64_t t0, int nb,
                                            const EmitCtx &e, int j) {
@@ -135,7 +113,7 @@ __device__ __forceinline__ void emit_slice(uint32_t *z, uint32_t *rb, const Keys
       for (int q = 0; q < 4; ++q) {
         const int l = 31 - k - 8 * q;
         if (e.stage && nb == 32)
-          rb[l * (kKsThreads * 4) + ((t0 >> 5) & 3)] = v[q];
+          rb[l * (kKsThreads * ST) + ((t0 >> 5) & (ST - 1))] = v[q];
         else if ((e.lane_mask >> l) & 1u)
           store_row_word<LAYOUT>(tile, pitch, f32_off, l, nb, e, v[q]);
       }
@@ -143,39 +121,42 @@ __device__ __forceinline__ void emit_slice(uint32_t *z, uint32_t *rb, const Keys
   }
 }
 
-template <int LAYOUT>
+template <int LAYOUT, int ST>
 __device__ __forceinline__ void emit_tile(uint32_t *z, uint32_t *rb, const KeystreamArgs &a,
                                           uint32_t g, uint64_t t0, int nb, const EmitCtx &e) {
 #pragma unroll 1
-  for (int j = 0; j < 8; ++j) emit_slice<LAYOUT>(z, rb, a, g, t0, nb, e, j);
+  for (int j = 0; j < 8; ++j) emit_slice<LAYOUT, ST>(z, rb, a, g, t0, nb, e, j);
 }
 
 // Row layouts with staging: write the staged words of tiles tA..tB (one
-// aligned block of four tiles, or part of one) of every valid row; a whole
-// block goes out as one 16-byte store per row (and per f32 row).
-template <int LAYOUT>
+// aligned block of ST tiles, or part of one) of every valid row; a whole
+// block goes out as ST/4 16-byte stores per row (and per f32 row).
+template <int LAYOUT, int ST>
 __device__ __forceinline__ void flush_rows(const uint32_t *rb, const KeystreamArgs &a,
                                            uint32_t g, uint32_t tA, uint32_t tB,
                                            const EmitCtx &e) {
   const uint32_t pitch = uint32_t(a.n_bits >> 3);
   uint8_t *base = static_cast<uint8_t *>(a.out) + 32ull * g * pitch + uint64_t(tA) * 4;
   const uint64_t f32_off = uint64_t(pitch) * a.n;
-  const int n = int(tB - tA) + 1, j0 = int(tA & 3);
+  const int n = int(tB - tA) + 1, j0 = int(tA & (ST - 1));
 #pragma unroll 1
   for (int l = 0; l < 32; ++l) {
     if (!((e.lane_mask >> l) & 1u)) continue;
-    const uint32_t *src = rb + l * (kKsThreads * 4);
+    const uint32_t *src = rb + l * (kKsThreads * ST);
     uint8_t *o = base + uint64_t(uint32_t(l) * pitch);
-    if (n == 4) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(src);
-      *reinterpret_cast<uint4 *>(o) = v;
-      if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32) {
-        float4 f;
-        f.x = __uint2float_rn(v.x >> 8) * 0x1p-24f;
-        f.y = __uint2float_rn(v.y >> 8) * 0x1p-24f;
-        f.z = __uint2float_rn(v.z >> 8) * 0x1p-24f;
-        f.w = __uint2float_rn(v.w >> 8) * 0x1p-24f;
-        *reinterpret_cast<float4 *>(o + f32_off) = f;
+    if (n == ST) {
+#pragma unroll
+      for (int h = 0; h < ST / 4; ++h) {
+        const uint4 v = reinterpret_cast<const uint4 *>(src)[h];
+        reinterpret_cast<uint4 *>(o)[h] = v;
+        if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32) {
+          float4 f;
+          f.x = __uint2float_rn(v.x >> 8) * 0x1p-24f;
+          f.y = __uint2float_rn(v.y >> 8) * 0x1p-24f;
+          f.z = __uint2float_rn(v.z >> 8) * 0x1p-24f;
+          f.w = __uint2float_rn(v.w >> 8) * 0x1p-24f;
+          reinterpret_cast<float4 *>(o + f32_off)[h] = f;
+        }
       }
     } else {
       for (int j = 0; j < n; ++j) {
@@ -194,7 +175,7 @@ __device__ __forceinline__ void flush_rows(const uint32_t *rb, const KeystreamAr
 // while the 32 clocks of tile k run (U clocks per step), the eight emission
 // slices of tile k-1 are interleaved with them, so the clock's independent
 // LOP3s hide the latency of the emission's shared-memory and global accesses.
-template <int LAYOUT, int U>
+template <int LAYOUT, int U, int ST>
 __device__ __forceinline__ void run_piece(const KeystreamArgs &a, EmitCtx e, uint32_t g,
                                           uint32_t *zbuf0, uint32_t *zbuf1, uint32_t *rb,
                                           uint32_t tile_a, uint32_t tile_b) {
@@ -223,15 +204,16 @@ __device__ __forceinline__ void run_piece(const KeystreamArgs &a, EmitCtx e, uin
         clock_kg<false, false>(r, s, 0u, 0u);
       }
       if (tile > tile_a && (c & 3) == 0)
-        emit_slice<LAYOUT>(prev, rb, a, g, uint64_t(tile - 1) << 5, 32, e, c >> 2);
+        emit_slice<LAYOUT, ST>(prev, rb, a, g, uint64_t(tile - 1) << 5, 32, e, c >> 2);
     }
-    if (LAYOUT != MICKEY_LAYOUT_BITSLICED_U32 && e.stage && tile > tile_a && ((tile - 1) & 3) == 3)
-      flush_rows<LAYOUT>(rb, a, g, max(tile - 4, tile_a), tile - 1, e);
+    if (LAYOUT != MICKEY_LAYOUT_BITSLICED_U32 && e.stage && tile > tile_a &&
+        ((tile - 1) & (ST - 1)) == ST - 1)
+      flush_rows<LAYOUT, ST>(rb, a, g, max(tile - ST, tile_a), tile - 1, e);
   }
   if (fend > tile_a) {
-    emit_tile<LAYOUT>((fend & 1) ? zbuf0 : zbuf1, rb, a, g, uint64_t(fend - 1) << 5, 32, e);
+    emit_tile<LAYOUT, ST>((fend & 1) ? zbuf0 : zbuf1, rb, a, g, uint64_t(fend - 1) << 5, 32, e);
     if (LAYOUT != MICKEY_LAYOUT_BITSLICED_U32 && e.stage)
-      flush_rows<LAYOUT>(rb, a, g, max((fend - 1) & ~3u, tile_a), fend - 1, e);
+      flush_rows<LAYOUT, ST>(rb, a, g, max((fend - 1) & ~uint32_t(ST - 1), tile_a), fend - 1, e);
   }
   if (tile_b > full && (a.n_bits & 31)) {  // the partial last tile
     uint32_t *cur = (full & 1) ? zbuf1 : zbuf0;
@@ -245,7 +227,7 @@ __device__ __forceinline__ void run_piece(const KeystreamArgs &a, EmitCtx e, uin
         cur[c * kKsThreads] = 0u;
       }
     }
-    emit_tile<LAYOUT>(cur, rb, a, g, uint64_t(full) << 5, rem, e);
+    emit_tile<LAYOUT, ST>(cur, rb, a, g, uint64_t(full) << 5, rem, e);
   }
 
   uint32_t *dst = a.state + g;
@@ -263,8 +245,8 @@ __global__ void __launch_bounds__(kKsThreads)
   extern __shared__ uint32_t zs[];
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.G) return;
-  run_piece<LAYOUT, U>(a, e, g, zs + threadIdx.x, zs + 32 * kKsThreads + threadIdx.x,
-                       zs + kTileBufWords + 4 * threadIdx.x, 0,
+  run_piece<LAYOUT, U, 4>(a, e, g, zs + threadIdx.x, zs + 32 * kKsThreads + threadIdx.x,
+                          zs + kTileBufWords + 4 * threadIdx.x, 0,
                        uint32_t((a.n_bits + 31) >> 5));
 }
 
@@ -354,8 +336,8 @@ __global__ void __launch_bounds__(kKsThreads, 1)
     }
     const uint32_t g = w * 32 + lane;
     if (g < a.G)
-      run_piece<LAYOUT, U>(a, e, g, zs + threadIdx.x, zs + 32 * kKsThreads + threadIdx.x,
-                           zs + kTileBufWords + 4 * threadIdx.x, ta, tb);
+      run_piece<LAYOUT, U, 8>(a, e, g, zs + threadIdx.x, zs + 32 * kKsThreads + threadIdx.x,
+                              zs + kTileBufWords + 8 * threadIdx.x, ta, tb);
     if (ta == 0 && tb < NT) {  // head: publish the state for the next segment
       __threadfence();
       __syncwarp();
@@ -364,23 +346,23 @@ __global__ void __launch_bounds__(kKsThreads, 1)
   }
 }
 
-size_t smem_bytes(const EmitCtx &e) {
-  return 4 * (kTileBufWords + (e.stage ? kRowStageWords : 0));
+size_t smem_bytes(const EmitCtx &e, int st) {
+  return 4 * (kTileBufWords + (e.stage ? row_stage_words(st) : 0));
 }
 
 template <class K>
-cudaError_t allow_smem(K kernel) {
+cudaError_t allow_smem(K kernel, int st) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(4 * (kTileBufWords + kRowStageWords)));
+                              int(4 * (kTileBufWords + row_stage_words(st))));
 }
 
 template <int LAYOUT, int U>
 cudaError_t launch_persistent(const KeystreamArgs &a, const EmitCtx &e, const PersistArgs &p,
                               cudaStream_t st) {
-  cudaError_t err = allow_smem(keystream_persistent_kernel<LAYOUT, U>);
+  cudaError_t err = allow_smem(keystream_persistent_kernel<LAYOUT, U>, 8);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};
-  cfg.dynamicSmemBytes = smem_bytes(e);
+  cfg.dynamicSmemBytes = smem_bytes(e, 8);
   cfg.gridDim = dim3(p.blocks);
   cfg.blockDim = dim3(kKsThreads);
   cfg.stream = st;
@@ -402,15 +384,15 @@ cudaError_t launch_layout(const KeystreamArgs &a, int unroll, const EmitCtx &e,
     return err != cudaSuccess ? err : cudaGetLastError();
   }
   const uint32_t blocks = (a.G + kKsThreads - 1) / kKsThreads;
-  const size_t smem = smem_bytes(e);
+  const size_t smem = smem_bytes(e, 4);
   cudaError_t err = cudaSuccess;
   switch (unroll) {
     case 2:
-      err = allow_smem(keystream_kernel<LAYOUT, 2>);
+      err = allow_smem(keystream_kernel<LAYOUT, 2>, 4);
       if (err == cudaSuccess) keystream_kernel<LAYOUT, 2><<<blocks, kKsThreads, smem, st>>>(a, e);
       break;
     case 4:
-      err = allow_smem(keystream_kernel<LAYOUT, 4>);
+      err = allow_smem(keystream_kernel<LAYOUT, 4>, 4);
       if (err == cudaSuccess) keystream_kernel<LAYOUT, 4><<<blocks, kKsThreads, smem, st>>>(a, e);
       break;
     default: return cudaErrorInvalidValue;
@@ -429,7 +411,7 @@ cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll, boo
   e.vec_ok = (addr % 16 == 0) && (a.n_bits % 4 == 0);
   e.word_ok = (addr % 4 == 0) && (((a.n_bits + 7) / 8) % 4 == 0);
   e.stage = stage && layout != MICKEY_LAYOUT_BITSLICED_U32 && (addr % 16 == 0) &&
-            (a.n_bits % 128 == 0);
+            (a.n_bits % (p ? 256 : 128) == 0);
   switch (layout) {
     case MICKEY_LAYOUT_BITSLICED_U32:
       return launch_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, unroll, e, p, st);

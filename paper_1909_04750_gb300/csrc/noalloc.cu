@@ -87,7 +87,7 @@ extern "C" MICKEY_API int mickey_init_state_noalloc(const uint8_t *keys, const u
       return MICKEY_E_CUDA;
     lens = reinterpret_cast<const uint32_t *>(in + n * 20);
   }
-  LoadArgs la{in, in + n * 10, lens, n, G, Gpad, rows, err};
+  LoadArgs la{in, in + n * 10, lens, n, nullptr, G, Gpad, rows, err};
   if (launch_load(la, st) != cudaSuccess) return MICKEY_E_CUDA;
   PreclockArgs pa{rows, state, G, Gpad};
   if (launch_preclock(pa, st) != cudaSuccess) return MICKEY_E_CUDA;
