@@ -246,6 +246,47 @@ MICKEY_API int mickey_batch_sync(mickey_batch *b);
 MICKEY_API void mickey_batch_free(mickey_batch *b);
 
 /* --------------------------------------------------------------------------
+ * Serving: continuous batching over resident streams.  The server keeps one
+ * 200-bit state row per stream id in device memory, so a follow-up request
+ * of a stream continues its keystream without reloading the key and IV.  A
+ * host scheduler (paper_1909_04750_gb300/serve.py) admits requests, packs
+ * the active ones into 32-lane groups and issues steps; each step is one
+ * launch that gathers the groups' states from the table, clocks them and
+ * writes each request's bytes to its own buffer, then scatters the states
+ * back.  Row format: words 0..3 hold R, words 4..7 hold S, register bit i at
+ * bit (31 - i % 32) of word i / 32 of its half.
+ * ------------------------------------------------------------------------ */
+typedef struct mickey_server mickey_server;
+
+/* Table of max_streams rows; up to max_groups groups per step.  NULL on
+ * error (mickey_last_error). */
+MICKEY_API mickey_server *mickey_server_create(size_t max_streams, uint32_t max_groups,
+                                               void *cuda_stream);
+/* Key/IV loading and preclocks of n new streams (host keys, ivs: n x 10
+ * bytes; iv_lens: n values or NULL = 80); their states go to table rows
+ * stream_ids[i].  Asynchronous, ordered before the next step. */
+MICKEY_API int mickey_server_init_streams(mickey_server *s, const uint32_t *stream_ids,
+                                          const uint8_t *keys, const uint8_t *ivs,
+                                          const uint32_t *iv_lens, size_t n);
+/* One step over G groups (host arrays, copied): slot_stream[32G] stream id of
+ * each lane (0xffffffff: unused), slot_out[32G] device byte address where the
+ * lane's bits of this step go (0: unused), group_clocks[G] bits every lane of
+ * group g produces (a multiple of 8).  Groups 0..n_split-1 are each clocked
+ * by a whole warp (lower time per clock, for the longest requests).
+ * Asynchronous; returns after the arrays are staged. */
+MICKEY_API int mickey_server_step(mickey_server *s, uint32_t G, uint32_t n_split,
+                                  const uint32_t *slot_stream, const uint64_t *slot_out,
+                                  const uint32_t *group_clocks);
+/* Current states of the given streams in the 26-byte format of
+ * mickey_export_state (synchronises). */
+MICKEY_API int mickey_server_read_states(mickey_server *s, const uint32_t *stream_ids, size_t n,
+                                         uint8_t *states);
+/* Step kernel: clocks per inner step (2 or 4), blocks of 4 warps per SM (1 or 2). */
+MICKEY_API int mickey_server_set_config(mickey_server *s, int unroll, int blocks_per_sm);
+MICKEY_API int mickey_server_sync(mickey_server *s);
+MICKEY_API void mickey_server_free(mickey_server *s);
+
+/* --------------------------------------------------------------------------
  * Allocation-free key/IV loading.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory -- code
  * running inside an application whose own allocator owns the GPU's memory,

@@ -67,6 +67,15 @@ SIGNATURES = {
     "mickey_batch_get_config": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "mickey_batch_sync": (c_int, [c_void_p]),
     "mickey_batch_free": (None, [c_void_p]),
+    "mickey_server_create": (c_void_p, [c_size_t, ctypes.c_uint32, c_void_p]),
+    "mickey_server_init_streams": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                           c_size_t]),
+    "mickey_server_step": (c_int, [c_void_p, ctypes.c_uint32, ctypes.c_uint32, c_void_p,
+                                   c_void_p, c_void_p]),
+    "mickey_server_read_states": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p]),
+    "mickey_server_set_config": (c_int, [c_void_p, c_int, c_int]),
+    "mickey_server_sync": (c_int, [c_void_p]),
+    "mickey_server_free": (None, [c_void_p]),
     "mickey_init_state_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p,
                                           c_void_p]),
 }

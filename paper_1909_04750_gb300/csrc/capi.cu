@@ -265,6 +265,12 @@ int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
 
 namespace mickey {
 int set_error(int code, const char *msg) { return code ? fail(code, "%s", msg) : ok(); }
+
+const uint32_t *handle_state(const mickey_streams *s, uint32_t *G, uint32_t *Gpad) {
+  *G = s->G;
+  *Gpad = s->Gpad;
+  return s->d_state;
+}
 }  // namespace mickey
 
 extern "C" {

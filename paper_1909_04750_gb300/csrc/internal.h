@@ -60,6 +60,12 @@ struct KeystreamArgs {
 // clears it); returns `code`.
 int set_error(int code, const char *msg);
 
+}  // namespace mickey
+struct mickey_streams;
+namespace mickey {
+// Device state words of a handle (kStateRows x Gpad, word-major).
+const uint32_t *handle_state(const mickey_streams *s, uint32_t *G, uint32_t *Gpad);
+
 // Unroll factors compiled for the keystream kernel.
 constexpr int kUnrolls[] = {2, 4};
 // Largest n_bits of one keystream launch: a row of the row-major layouts
