@@ -37,58 +37,80 @@ def _server(n_streams, **kw):
     return Server(n_streams, **args)
 
 
-def _per_stream(jobs):
+def _per_stream(reqs, finish):
     out = {}
-    for j in jobs:
-        if not j.rejected:
-            out.setdefault(j.stream_id, []).append(j)
+    for j, r in enumerate(reqs):
+        if not np.isnan(finish[j]):
+            out.setdefault(r.stream_id, []).append(j)
     return out
 
 
-def _check_against_oracle(jobs):
-    for sid, js in _per_stream(jobs).items():
-        total = sum(j.n_bits for j in js)
-        j0 = js[0]
-        ref = oracle.stream(j0.key, j0.iv, j0.iv_len, total)
-        got = b"".join(j.buf[: j.n_bits // 8].cpu().numpy().tobytes() for j in js)
+def _check_against_oracle(srv, reqs, finish):
+    for sid, js in _per_stream(reqs, finish).items():
+        total = sum(8 * reqs[j].n_bytes for j in js)
+        r0 = reqs[js[0]]
+        ref = oracle.stream(r0.key, r0.iv, r0.iv_len, total)
+        got = b"".join(srv.outputs[j].cpu().numpy().tobytes() for j in js)
         assert got == ref, sid
 
 
 def test_served_trace_matches_oracle_and_states():
     reqs, keyset = _trace()
     srv = _server(keyset.n)
-    jobs = srv.run(reqs, realtime=False)
+    finish = srv.run(reqs, realtime=False)
     assert srv.stats["completed"] == len(reqs) and srv.steps > 3
-    _check_against_oracle(jobs)
+    _check_against_oracle(srv, reqs, finish)
     # resident states equal the oracle's state after each stream's bits
-    ids = sorted(_per_stream(jobs))[:6]
+    per = _per_stream(reqs, finish)
+    ids = sorted(per)[:6]
     states = srv.read_states(ids)
     for k, sid in enumerate(ids):
-        js = _per_stream(jobs)[sid]
-        st = oracle.init(js[0].key, js[0].iv, js[0].iv_len)
-        oracle.keystream_from(st, sum(j.n_bits for j in js))
+        js = per[sid]
+        r0 = reqs[js[0]]
+        st = oracle.init(r0.key, r0.iv, r0.iv_len)
+        oracle.keystream_from(st, sum(8 * reqs[j].n_bytes for j in js))
         r, s = st.bits()
         assert np.array_equal(states[k], np.concatenate([np.packbits(r), np.packbits(s)]))
 
 
 def test_request_same_alone_and_in_mix():
     reqs, keyset = _trace(seed=9)
-    mix = _server(keyset.n).run(reqs, realtime=False)
-    by = _per_stream(mix)
+    mix = _server(keyset.n)
+    fin = mix.run(reqs, realtime=False)
+    by = _per_stream(reqs, fin)
     sid = max(by, key=lambda k: len(by[k]))       # the stream with most requests
-    alone_reqs = [r for r in reqs if r.stream_id == sid]
-    alone = _server(keyset.n).run(alone_reqs, realtime=False)
-    for a, m in zip(alone, by[sid]):
-        assert a.n_bits == m.n_bits
-        assert torch.equal(a.buf[: a.n_bits // 8], m.buf[: m.n_bits // 8])
+    alone_reqs = [reqs[j] for j in by[sid]]
+    alone = _server(keyset.n)
+    alone.run(alone_reqs, realtime=False)
+    for a, m in enumerate(by[sid]):
+        assert torch.equal(alone.outputs[a], mix.outputs[m])
 
 
 def test_small_budget_still_correct():
     reqs, keyset = _trace(duration_s=0.02, seed=5)
-    srv = _server(keyset.n, budget_bytes=6000, max_inflight=1)
-    jobs = srv.run(reqs, realtime=False)
+    srv = _server(keyset.n, budget_bytes=6000 + 32 * keyset.n, max_inflight=1)
+    finish = srv.run(reqs, realtime=False)
     assert srv.stats["completed"] == len(reqs)
-    _check_against_oracle(jobs)
+    _check_against_oracle(srv, reqs, finish)
+
+
+def test_streaming_outputs_and_stats():
+    # response chunks go to per-step arenas under the budget
+    reqs, keyset = _trace(duration_s=0.03, seed=8)
+    srv = _server(keyset.n, keep_outputs=False, budget_bytes=(1 << 20) + 32 * keyset.n)
+    finish = srv.run(reqs, realtime=False)
+    st = srv.stats
+    assert st["completed"] == len(reqs) and st["served_bits"] == sum(8 * r.n_bytes for r in reqs)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    # states still advanced exactly
+    per = _per_stream(reqs, finish)
+    sid = sorted(per)[0]
+    r0 = reqs[per[sid][0]]
+    ost = oracle.init(r0.key, r0.iv, r0.iv_len)
+    oracle.keystream_from(ost, sum(8 * reqs[j].n_bytes for j in per[sid]))
+    r, s = ost.bits()
+    assert np.array_equal(srv.read_states([sid])[0], np.concatenate([np.packbits(r),
+                                                                    np.packbits(s)]))
 
 
 def test_changed_key_for_resident_stream_is_rejected():
@@ -96,6 +118,6 @@ def test_changed_key_for_resident_stream_is_rejected():
     r0 = reqs[0]
     bad = workloads.Request(r0.arrival_s + 1e-3, r0.stream_id, bytes(10), r0.iv, r0.iv_len, 64)
     srv = _server(keyset.n)
-    jobs = srv.run(reqs + [bad], realtime=False)
-    assert jobs[-1].rejected and srv.stats["rejected"] == 1
-    _check_against_oracle(jobs)
+    finish = srv.run(reqs + [bad], realtime=False)
+    assert np.isnan(finish[-1]) and srv.stats["rejected"] == 1
+    _check_against_oracle(srv, reqs, finish[:-1])
