@@ -99,8 +99,8 @@ def _time(batch, keys, ivs, out) -> float:
 
 def tune(batch: Batch, keys, ivs, out: torch.Tensor, refresh: bool = False) -> dict:
     """Pick the split threshold (groups longer than it run one per warp), the
-    clocks per step and the blocks per SM by timing whole runs; cached per
-    GPU and batch shape."""
+    blocks per SM and the unroll depth by timing whole runs; cached per GPU
+    and batch shape."""
     key = shape_key(batch)
     with _lock:
         hit = None if refresh else _load().get(key)
@@ -115,11 +115,17 @@ def tune(batch: Batch, keys, ivs, out: torch.Tensor, refresh: bool = False) -> d
         cands.append(c)
         return c
 
+    # the longest groups bound the run (one clock after another), so the
+    # split threshold and the warps per SM sub-partition (which share its
+    # issue slots with the critical group's warp) are searched together
     mx = batch.max_clocks
-    best = min((trial(4, 2, sc) for sc in (0, mx // 4, mx // 8, mx // 16, mx // 32)),
-               key=lambda c: c["ms"])
-    for u, b in ((2, 2), (4, 1), (2, 1)):
-        trial(u, b, best["split_clocks"])
+    for b in (1, 2):
+        # no split path at all only where the longest group is short
+        for sc in ((0,) if mx <= 1 << 16 else ()) + (mx // 4, mx // 8, mx // 16, mx // 32,
+                                                     mx // 64):
+            trial(4, b, sc)
+    best = min(cands, key=lambda c: c["ms"])
+    trial(2, best["blocks_per_sm"], best["split_clocks"])
     best = min(cands, key=lambda c: c["ms"])
     batch.set_config(best["unroll"], best["blocks_per_sm"], best["split_clocks"])
     entry = dict(best, candidates=cands)

@@ -7,8 +7,8 @@ one persistent launch replayed from a CUDA graph.
 Prints one JSON line: Gbit/s over all streams, and the two lower bounds on a
 run's time -- the work at the plain kernel's measured rate, and the critical
 path (the longest group's clocks at the measured time per clock of a group
-running alone; MICKEY has no jump-ahead, so a stream's bits are produced one
-clock after another).
+clocked alone by one warp; MICKEY has no jump-ahead, so a stream's bits are
+produced one clock after another).
 """
 import argparse
 import json
@@ -20,6 +20,24 @@ from . import workloads
 from .batch import Batch, tune
 from .build import build
 from .streams import Streams
+
+
+def lone_split_ns_per_clock(n_bits: int = 1 << 18) -> float:
+    """Time per clock of one 32-lane group clocked alone by one warp."""
+    s = workloads.plain_scale(32)
+    b = Batch(np.full(32, n_bits, np.uint64))
+    b.set_config(4, 1, 1)
+    k, v = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
+    out = torch.empty(b.output_bytes, dtype=torch.uint8, device="cuda")
+    b.run(k, v, out)
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.run(k, v, out)
+    e1.record(b.stream)
+    b.sync()
+    b.free()
+    return e0.elapsed_time(e1) * 1e6 / n_bits
 
 
 def lone_group_ns_per_clock(n_bits: int = 1 << 16) -> float:
@@ -61,15 +79,19 @@ def main():
         times.append(e0.elapsed_time(e1))
     ms = min(times)
     bits = int(s.n_bits.sum())
-    t_clk = lone_group_ns_per_clock()
+    t_thread = lone_group_ns_per_clock()
+    t_clk = lone_split_ns_per_clock()
     crit_ms = b.max_clocks * t_clk * 1e-6
     line = {
         "metric": "batched keystream Gbit/s (100k ragged streams, one persistent launch)",
         "value": bits / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms_per_run": ms,
         "runs": a.runs, "streams": b.n, "keystream_bits": bits,
         "groups_clocks_total": b.total_clocks, "longest_group_clocks": b.max_clocks,
-        "lone_group_ns_per_clock": t_clk, "critical_path_ms": crit_ms,
-        "config": {"unroll": tuned["unroll"], "blocks_per_sm": tuned["blocks_per_sm"]},
+        "lone_split_ns_per_clock": t_clk, "lone_thread_group_ns_per_clock": t_thread,
+        "critical_path_ms": crit_ms, "frac_of_critical_path": crit_ms / ms,
+        "config": {"unroll": tuned["unroll"], "blocks_per_sm": tuned["blocks_per_sm"],
+                   "split_clocks": tuned["split_clocks"],
+                   "split_groups": tuned.get("split_groups")},
     }
     if a.plain_gbit_s:
         line["work_bound_ms"] = bits / (a.plain_gbit_s * 1e9) * 1e3

@@ -151,51 +151,49 @@ __device__ __forceinline__ void batch_group(const BatchArgs &a, uint8_t *out, ui
   }
 }
 
-// Emit a 32-clock tile: lane c holds the keystream word of clock c (zt);
-// 32 ballots give lane l its instance's bits, clock c in bit c, which are
-// reversed (z of the tile's first clock first) and put in memory byte order.
-__device__ __forceinline__ void split_emit(uint32_t zt, uint8_t *out, const BatchArgs &a,
-                                           uint32_t g, uint32_t lane, uint32_t t) {
-  uint32_t mine = 0;
-#pragma unroll
-  for (int l = 0; l < 32; ++l) {
-    const uint32_t w = __ballot_sync(0xffffffffu, (zt >> l) & 1u);
-    mine = lane == uint32_t(l) ? w : mine;
+// Store word w (memory byte order) of tile t of a row at o with `bits`
+// keystream bits (split path: row address and length held in registers).
+__device__ __forceinline__ void store_row(uint8_t *o, uint64_t bits, uint32_t t, uint32_t w) {
+  const uint64_t b0 = uint64_t(t) << 5;
+  if (b0 >= bits) return;
+  o += b0 >> 3;
+  const uint64_t left = bits - b0;
+  if (left >= 32) {
+    *reinterpret_cast<uint32_t *>(o) = w;
+    return;
   }
-  store_ragged(out, a, uint64_t(g) * 32 + lane, t, __byte_perm(__brev(mine), 0u, 0x0123));
+  w &= __byte_perm(~0u << (32 - uint32_t(left)), 0u, 0x0123);
+  const int nbytes = int((left + 7) >> 3);
+  for (int b = 0; b < nbytes; ++b) o[b] = uint8_t(w >> (8 * b));
 }
 
-__device__ __forceinline__ void split_group(const BatchArgs &a, uint8_t *out, uint32_t g,
-                                            uint32_t lane) {
+// One warp per group (split path); the tile's bits come back transposed
+// (clock c in bit c of lane l's word), reversed so that the tile's first
+// clock comes first, and put in memory byte order.
+__device__ __forceinline__ void split_group(const uint32_t *state, size_t P, uint32_t g,
+                                            uint64_t clocks, uint8_t *row, uint64_t bits,
+                                            uint32_t lane, uint32_t *zbuf) {
   SplitLane k;
-  split_lane_masks(lane, k);
-  const size_t P = a.Gpad;
+  split_lane_init(lane, k);
   uint32_t r[4], s[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = int(4 * lane) + q;
-    r[q] = i < kReg ? a.state[size_t(i) * P + g] : 0u;
-    s[q] = i < kReg ? a.state[size_t(kReg + i) * P + g] : 0u;
+    r[q] = i < kReg ? state[size_t(i) * P + g] : 0u;
+    s[q] = i < kReg ? state[size_t(kReg + i) * P + g] : 0u;
   }
-  const uint64_t clocks = a.group_bits[g];
   const uint32_t full = uint32_t(clocks >> 5);
 #pragma unroll 1
   for (uint32_t t = 0; t < full; ++t) {
-    uint32_t zt = 0;
-#pragma unroll 1
-    for (int c = 0; c < 32; c += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) split_step(r, s, k, lane, c + u, zt);
-    }
-    split_emit(zt, out, a, g, lane, t);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, 32);
+    store_row(row, bits, t, __byte_perm(__brev(mine), 0u, 0x0123));
   }
   const int rem = int(clocks & 31);
   if (rem) {
-    uint32_t zt = 0;
-#pragma unroll 1
-    for (int c = 0; c < rem; ++c) split_step(r, s, k, lane, c, zt);
-    split_emit(zt, out, a, g, lane, full);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, rem);
+    store_row(row, bits, full, __byte_perm(__brev(mine), 0u, 0x0123));
   }
+  __syncwarp();
 }
 
 // Work items in queue order: first one item per split group (groups
@@ -213,7 +211,10 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
     if (item < a.n_split) {
-      split_group(a, out, item, lane);
+      // the warp's own 32 columns of row 0 of the tile buffer
+      const uint64_t slot = uint64_t(item) * 32 + lane;
+      split_group(a.state, a.Gpad, item, a.group_bits[item], out + a.slot_off[slot],
+                  a.slot_bits[slot], lane, zs + (threadIdx.x & ~31u));
       continue;
     }
     const uint32_t g = a.n_split + (item - a.n_split) * 32 + lane;

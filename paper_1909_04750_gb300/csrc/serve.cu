@@ -10,9 +10,12 @@
 // smallest remaining length of the group's requests, capped by a quantum, so
 // no request overshoots).  The kernel gathers each group's bitsliced state
 // from the table, clocks it, and scatters it back.  Groups 0..n_split-1 (the
-// longest remaining work) are clocked by a whole warp each (split path); the
-// rest one group per thread, 32 groups per work item, from an atomic queue.
+// longest remaining work) are clocked by a whole warp each (split path, a
+// kernel of their own); the rest one group per thread, 32 groups per work
+// item, from an atomic queue, in a second kernel after it on the stream.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include <cstring>
 #include <new>
@@ -169,7 +172,8 @@ __device__ __forceinline__ void serve_group(const ServeArgs &a, uint32_t g, uint
 
 // Split path: lane l brings its stream's row; 200 ballots give lane j the
 // bitsliced words of its register bits 4j..4j+3.
-__device__ __forceinline__ void serve_split(const ServeArgs &a, uint32_t g, uint32_t lane) {
+__device__ __forceinline__ void serve_split(const ServeArgs &a, uint32_t g, uint32_t lane,
+                                            uint32_t *zbuf) {
   const uint32_t st = a.slot_stream[uint64_t(g) * 32 + lane];
   uint32_t row[8];
 #pragma unroll
@@ -185,36 +189,19 @@ __device__ __forceinline__ void serve_split(const ServeArgs &a, uint32_t g, uint
     }
   }
   SplitLane k;
-  split_lane_masks(lane, k);
+  split_lane_init(lane, k);
   const uint64_t base = a.slot_out[uint64_t(g) * 32 + lane];
   const uint32_t clocks = a.group_clocks[g];
   const uint32_t full = clocks >> 5;
-  auto emit = [&](uint32_t zt, uint32_t t, int nb) {
-    uint32_t mine = 0;
-#pragma unroll
-    for (int l = 0; l < 32; ++l) {
-      const uint32_t w = __ballot_sync(0xffffffffu, (zt >> l) & 1u);
-      mine = lane == uint32_t(l) ? w : mine;
-    }
-    store_lane(base, t, nb, __byte_perm(__brev(mine), 0u, 0x0123));
-  };
 #pragma unroll 1
   for (uint32_t t = 0; t < full; ++t) {
-    uint32_t zt = 0;
-#pragma unroll 1
-    for (int c = 0; c < 32; c += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) split_step(r, s, k, lane, c + u, zt);
-    }
-    emit(zt, t, 32);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, 32);
+    store_lane(base, t, 32, __byte_perm(__brev(mine), 0u, 0x0123));
   }
   const int rem = int(clocks & 31);
   if (rem) {
-    uint32_t zt = 0;
-#pragma unroll 1
-    for (int c = 0; c < rem; ++c) split_step(r, s, k, lane, c, zt);
-    // lanes c >= rem hold zt = 0, so the tile's unused clocks read as zero
-    emit(zt, full, rem);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, rem);
+    store_lane(base, full, rem, __byte_perm(__brev(mine), 0u, 0x0123));
   }
   // back to rows: word of bit i is held by lane i/4
   uint32_t out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -231,6 +218,7 @@ __device__ __forceinline__ void serve_split(const ServeArgs &a, uint32_t g, uint
   }
 }
 
+// One group per thread, 32 groups per work item, from the atomic queue.
 template <int U>
 __global__ void __launch_bounds__(kServeThreads) serve_step_kernel(ServeArgs a) {
   __shared__ uint32_t zs[32 * kServeThreads];
@@ -241,12 +229,27 @@ __global__ void __launch_bounds__(kServeThreads) serve_step_kernel(ServeArgs a) 
     if (lane == 0) item = atomicAdd(a.queue, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
-    if (item < a.n_split) {
-      serve_split(a, item, lane);
-      continue;
-    }
-    const uint32_t g = a.n_split + (item - a.n_split) * 32 + lane;
+    const uint32_t g = item * 32 + lane;
     if (g < a.G) serve_group<U>(a, g, zs + threadIdx.x);
+  }
+}
+
+// Split groups only (a step's groups 0 .. n_split-1), with a register
+// budget of its own: the one-thread-per-group path needs the whole register
+// file of a thread, which limits a combined kernel to 2 warps per SM
+// sub-partition; this one runs at least 4.
+constexpr int kSplitMinBlocksPerSm = 4;
+__global__ void __launch_bounds__(kServeThreads, kSplitMinBlocksPerSm)
+    serve_split_kernel(ServeArgs a) {
+  __shared__ uint32_t zs[kServeThreads];   // 32 words per warp
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll 1
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(a.queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= a.n_split) break;
+    serve_split(a, item, lane, zs + (threadIdx.x & ~31u));
   }
 }
 
@@ -280,7 +283,7 @@ struct mickey_server {
   size_t max_streams = 0;
   uint32_t max_groups = 0;
   cudaStream_t stream = nullptr;
-  int sm_count = 0, unroll = 4, blocks_per_sm = 2;
+  int sm_count = 0, unroll = 4, blocks_per_sm = 2, split_blocks_per_sm = kSplitMinBlocksPerSm;
   uint32_t *d_packed = nullptr;
   // per-step metadata, double buffered: slot_stream, slot_out, group_clocks, queue
   struct Meta {
@@ -339,13 +342,18 @@ MICKEY_API mickey_server *mickey_server_create(size_t max_streams, uint32_t max_
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, serve_split_kernel, kServeThreads, 0) ==
+          cudaSuccess &&
+      nb > 0)
+    s->split_blocks_per_sm = nb;
   bool ok = cudaMalloc(&s->d_packed, max_streams * 32) == cudaSuccess &&
             cudaMemset(s->d_packed, 0, max_streams * 32) == cudaSuccess;
   for (auto &m : s->meta) {
     ok = ok && cudaMalloc(&m.d_stream, size_t(max_groups) * 32 * 4) == cudaSuccess &&
          cudaMalloc(&m.d_out, size_t(max_groups) * 32 * 8) == cudaSuccess &&
          cudaMalloc(&m.d_clocks, size_t(max_groups) * 4) == cudaSuccess &&
-         cudaMalloc(&m.d_queue, 4) == cudaSuccess &&
+         cudaMalloc(&m.d_queue, 8) == cudaSuccess &&
          cudaMallocHost(&m.h_stage, meta_bytes(max_groups)) == cudaSuccess &&
          cudaEventCreateWithFlags(&m.done, cudaEventDisableTiming) == cudaSuccess;
   }
@@ -431,16 +439,30 @@ MICKEY_API int mickey_server_step(mickey_server *s, uint32_t G, uint32_t n_split
       cudaMemcpyAsync(m.d_out, h + ns, no, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
       cudaMemcpyAsync(m.d_clocks, h + ns + no, nc, cudaMemcpyHostToDevice, s->stream) !=
           cudaSuccess ||
-      cudaMemsetAsync(m.d_queue, 0, 4, s->stream) != cudaSuccess)
+      cudaMemsetAsync(m.d_queue, 0, 8, s->stream) != cudaSuccess)
     return set_error(MICKEY_E_CUDA, "step upload");
-  ServeArgs a{s->d_packed, m.d_stream, m.d_out, m.d_clocks, G, n_split,
-              n_split + (G - n_split + 31) / 32, m.d_queue};
-  const uint32_t grid = uint32_t(s->sm_count * s->blocks_per_sm);
-  if (s->unroll == 2)
-    serve_step_kernel<2><<<grid, kServeThreads, 0, s->stream>>>(a);
-  else
-    serve_step_kernel<4><<<grid, kServeThreads, 0, s->stream>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return set_error(MICKEY_E_CUDA, "step kernel");
+  // split groups: their own kernel, up to 4 warps per SM sub-partition
+  if (n_split) {
+    ServeArgs a{s->d_packed, m.d_stream, m.d_out, m.d_clocks, n_split, n_split, n_split,
+                m.d_queue};
+    const uint32_t warps = kServeThreads / 32;
+    const uint32_t grid = std::min<uint32_t>((n_split + warps - 1) / warps,
+                                             uint32_t(s->sm_count * s->split_blocks_per_sm));
+    serve_split_kernel<<<grid, kServeThreads, 0, s->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return set_error(MICKEY_E_CUDA, "split kernel");
+  }
+  // the rest one group per thread, after them on the stream
+  if (G > n_split) {
+    const uint32_t Gt = G - n_split;
+    ServeArgs a{s->d_packed, m.d_stream + size_t(n_split) * 32, m.d_out + size_t(n_split) * 32,
+                m.d_clocks + n_split, Gt, 0, (Gt + 31) / 32, m.d_queue + 1};
+    const uint32_t grid = uint32_t(s->sm_count * s->blocks_per_sm);
+    if (s->unroll == 2)
+      serve_step_kernel<2><<<grid, kServeThreads, 0, s->stream>>>(a);
+    else
+      serve_step_kernel<4><<<grid, kServeThreads, 0, s->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return set_error(MICKEY_E_CUDA, "step kernel");
+  }
   if (cudaEventRecord(m.done, s->stream) != cudaSuccess) return set_error(MICKEY_E_CUDA, "event");
   return set_error(MICKEY_OK, "");
 }

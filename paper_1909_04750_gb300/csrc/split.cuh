@@ -8,15 +8,24 @@
 
 namespace mickey {
 
-// Split path for long groups: one warp clocks one group, so a clock costs
-// about 34 logic ops per lane instead of ~390 per thread.  Lane j (< 25) owns
-// register bits 4j .. 4j+3 of R and of S (slots 0..3); lanes 25..31 carry
-// no bits.  Each clock the warp exchanges neighbour words (r_{4j-1},
-// s_{4j-1}, s_{4j+4}) and broadcasts the control and feedback words (s34,
-// r67, s67, r33, r99, s99) with shuffles; the table constants become per-lane
-// masks.  The keystream word z = r0 ^ s0 (lane 0) is broadcast each clock
-// and kept by lane c for clock c; every 32 clocks 32 ballots give each lane
-// its instance's 32 bits.
+// Split path for long groups, where the time per clock of one group (and
+// not the throughput of many) bounds the run.  Lane j < 25 owns register
+// bits 4j .. 4j+3 of R and of S (slots 0..3); lanes 25..31 hold zeros that
+// stay zero.  One clock per lane:
+//   * 9 shuffles: the neighbour words r_{4j-1}, s_{4j-1}, s_{4j+4} and the
+//     control / feedback words s34, r67, s67, r33, r99, s99;
+//   * R: r'_i = r_{i-1} ^ (CBR & r_i) ^ (fb_R & [i in RTAPS]), 2 LOP3 a slot;
+//   * S: the table constants of bit i are lane-dependent, so the terms that
+//     XOR or AND a word with one of them, s_i ^ COMP0_i (zero outside
+//     i = 1..98), s_{i+1} ^ COMP1_i and FB0_i ^ (CBS & (FB0_i ^ FB1_i)), are
+//     each x * m + a with m in {0, 1, -1} and a in {0, -1} (IMAD, on the FMA
+//     pipe beside the logic pipe); two LOP3 combine them.
+// Lane 0 stores z = r0 ^ s0 (computed before the clock) to the warp's 32
+// words of shared memory; after 32 clocks a 5-stage xor-shuffle butterfly
+// transposes the 32 x 32 bit tile, so lane l holds its instance's 32 bits.
+
+// clocks per iteration of the split path's tile loop
+constexpr int kSplitUnroll = 8;
 
 struct SplitMasks {
   uint32_t rtap[4], comp0[4], comp1[4], fb0[4], fb1[4];
@@ -40,36 +49,52 @@ __device__ __forceinline__ uint32_t bit_mask(const uint32_t (&w)[4], int i) {
 }
 
 struct SplitLane {
-  uint32_t tap[4], c0[4], c1[4], en[4], fb0[4], fb1[4];
+  uint32_t src_up, src_dn;                       // shuffle sources of the neighbour words
+  uint32_t tap[4];                               // RTAPS as 0 / ~0
+  uint32_t c0m[4], c0a[4], c1m[4], c1a[4], fbm[4], fba[4];   // IMAD coefficients
+  uint32_t tmask[5], tshift[5];                  // butterfly transpose stages
 };
 
-__device__ __forceinline__ void split_lane_masks(uint32_t lane, SplitLane &k) {
+__device__ __forceinline__ void split_lane_init(uint32_t lane, SplitLane &k) {
+  // lane 0 reads lane 31 (zero) for r_{-1} = s_{-1} = 0; the zero lanes
+  // read themselves, so nothing ever reaches them
+  k.src_up = lane == 0 ? 31u : (lane >= 25 ? lane : lane - 1);
+  k.src_dn = (lane + 1) & 31u;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = int(4 * lane) + q;
     k.tap[q] = bit_mask(kSplitMasks.rtap, i);
-    k.c0[q] = bit_mask(kSplitMasks.comp0, i);
-    k.c1[q] = bit_mask(kSplitMasks.comp1, i);
-    k.fb0[q] = bit_mask(kSplitMasks.fb0, i);
-    k.fb1[q] = bit_mask(kSplitMasks.fb1, i);
-    // non-linear term of s^_i exists for i = 1..98 only
-    k.en[q] = (i >= 1 && i <= 98) ? ~0u : 0u;
+    const uint32_t c0 = bit_mask(kSplitMasks.comp0, i), c1 = bit_mask(kSplitMasks.comp1, i);
+    const uint32_t f0 = bit_mask(kSplitMasks.fb0, i), f1 = bit_mask(kSplitMasks.fb1, i);
+    const bool en = i >= 1 && i <= 98;          // the non-linear term exists for 1..98
+    k.c0m[q] = en ? (c0 ? ~0u : 1u) : 0u;       // (s ^ c0) & en
+    k.c0a[q] = en ? c0 : 0u;
+    k.c1m[q] = c1 ? ~0u : 1u;                   // x ^ c1
+    k.c1a[q] = c1;
+    k.fbm[q] = (f0 ^ f1) ? (f0 ? ~0u : 1u) : 0u;   // f0 ^ (cbs & (f0 ^ f1))
+    k.fba[q] = f0;
+  }
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const uint32_t j = 16u >> st;
+    constexpr uint32_t kLow[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+    const bool top = (lane & j) == 0;
+    k.tmask[st] = top ? kLow[st] : ~kLow[st];
+    k.tshift[st] = top ? j : 32u - j;
   }
 }
 
 // One non-mixing CLOCK_KG of the group spread over the warp.
-__device__ __forceinline__ void clock_split(uint32_t (&r)[4], uint32_t (&s)[4], const SplitLane &k,
-                                            uint32_t lane) {
+__device__ __forceinline__ void clock_split(uint32_t (&r)[4], uint32_t (&s)[4],
+                                            const SplitLane &k) {
   constexpr uint32_t F = 0xffffffffu;
-  const uint32_t up_ok = lane ? ~0u : 0u;
-  const uint32_t r_up = __shfl_up_sync(F, r[3], 1) & up_ok;   // r_{4j-1} (r_{-1} = 0)
-  const uint32_t s_up = __shfl_up_sync(F, s[3], 1) & up_ok;   // s_{4j-1}
-  const uint32_t s_dn = __shfl_down_sync(F, s[0], 1);         // s_{4j+4}
+  const uint32_t r_up = __shfl_sync(F, r[3], k.src_up);
+  const uint32_t s_up = __shfl_sync(F, s[3], k.src_up);
+  const uint32_t s_dn = __shfl_sync(F, s[0], k.src_dn);
   const uint32_t cbr = __shfl_sync(F, s[2], 8) ^ __shfl_sync(F, r[3], 16);   // s34 ^ r67
   const uint32_t cbs = __shfl_sync(F, s[3], 16) ^ __shfl_sync(F, r[1], 8);   // s67 ^ r33
   const uint32_t fbr = __shfl_sync(F, r[3], 24);                              // r99
   const uint32_t fbs = __shfl_sync(F, s[3], 24);                              // s99
-  const uint32_t f0 = fbs & ~cbs, f1 = fbs & cbs;
   uint32_t nr[4], ns[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -77,11 +102,10 @@ __device__ __forceinline__ void clock_split(uint32_t (&r)[4], uint32_t (&s)[4], 
     nr[q] = rm1 ^ (cbr & r[q]) ^ (fbr & k.tap[q]);
     const uint32_t sm1 = q ? s[q - 1] : s_up;
     const uint32_t sp1 = q < 3 ? s[q + 1] : s_dn;
-    // bits 0 and 99 (no non-linear term) sit in slots 0 and 3 only; the
-    // dummy lanes' results never reach a real bit
-    const uint32_t a = (q == 0 || q == 3) ? ((s[q] ^ k.c0[q]) & k.en[q]) : (s[q] ^ k.c0[q]);
-    const uint32_t nl = a & (sp1 ^ k.c1[q]);
-    ns[q] = sm1 ^ nl ^ (f0 & k.fb0[q]) ^ (f1 & k.fb1[q]);
+    const uint32_t y = s[q] * k.c0m[q] + k.c0a[q];
+    const uint32_t z = sp1 * k.c1m[q] + k.c1a[q];
+    const uint32_t sel = cbs * k.fbm[q] + k.fba[q];
+    ns[q] = sm1 ^ (y & z) ^ (fbs & sel);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -90,12 +114,39 @@ __device__ __forceinline__ void clock_split(uint32_t (&r)[4], uint32_t (&s)[4], 
   }
 }
 
-// One clock plus keeping z = r0 ^ s0 (lane 0's slot 0) of clock c in lane c.
-__device__ __forceinline__ void split_step(uint32_t (&r)[4], uint32_t (&s)[4], const SplitLane &k,
-                                           uint32_t lane, int c, uint32_t &zt) {
-  const uint32_t z = __shfl_sync(0xffffffffu, r[0] ^ s[0], 0);
-  zt = lane == uint32_t(c) ? z : zt;
-  clock_split(r, s, k, lane);
+// n <= 32 clocks of the group (z of clock c to zbuf[c] by lane 0), then the
+// transpose: returns lane's instance's bits, clock c in bit c (bits >= n
+// zero).  zbuf: 32 words of shared memory owned by the warp.
+template <int SU>
+__device__ __forceinline__ uint32_t split_tile(uint32_t (&r)[4], uint32_t (&s)[4],
+                                               const SplitLane &k, uint32_t lane,
+                                               uint32_t *zbuf, int n) {
+  const bool lead = lane == 0;
+  if (n == 32) {
+#pragma unroll 1
+    for (int c = 0; c < 32; c += SU) {
+#pragma unroll
+      for (int u = 0; u < SU; ++u) {
+        if (lead) zbuf[c + u] = r[0] ^ s[0];
+        clock_split(r, s, k);
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < n; ++c) {
+      if (lead) zbuf[c] = r[0] ^ s[0];
+      clock_split(r, s, k);
+    }
+  }
+  __syncwarp();
+  uint32_t x = lane < uint32_t(n) ? zbuf[lane] : 0u;
+  __syncwarp();
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, 16 >> st);
+    x = (x & k.tmask[st]) | (__funnelshift_l(y, y, k.tshift[st]) & ~k.tmask[st]);
+  }
+  return x;
 }
 
 }  // namespace mickey

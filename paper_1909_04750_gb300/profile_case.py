@@ -1,11 +1,15 @@
 """Run one workload shape through the library, for profilers.
 
     python -m paper_1909_04750_gb300.profile_case --n 1048576 --n-bits 2048 --layout bytes
+    python -m paper_1909_04750_gb300.profile_case --case split --n 32 --n-bits 65536
 
-Creates a handle for ``workloads.plain_scale(n)`` (device inputs), then
-``--reps`` times re-keys it and generates ``n_bits`` per stream in
-``layout``.  The launch configuration comes from the environment
+``plain``: creates a handle for ``workloads.plain_scale(n)`` (device
+inputs), then ``--reps`` times re-keys it and generates ``n_bits`` per
+stream in ``layout``.  The launch configuration comes from the environment
 (MICKEY_MODE, MICKEY_UNROLL, MICKEY_STAGE) or the library defaults.
+
+``split``: a batch of n streams of ``n_bits`` each whose groups all take the
+one-warp-per-group path (split threshold 1 clock), run ``--reps`` times.
 """
 import argparse
 
@@ -22,8 +26,22 @@ def main():
     p.add_argument("--n-bits", type=int, default=2048)
     p.add_argument("--layout", default="bytes")
     p.add_argument("--reps", type=int, default=2)
+    p.add_argument("--case", choices=("plain", "split"), default="plain")
     a = p.parse_args()
     build()
+    if a.case == "split":
+        import numpy as np
+        from .batch import Batch
+        s = workloads.plain_scale(a.n)
+        b = Batch(np.full(a.n, a.n_bits, np.uint64))
+        b.set_config(4, 1, 1)
+        k, v = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
+        out = torch.empty(b.output_bytes, dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            b.run(k, v, out)
+        b.sync()
+        print("ok", vars(a))
+        return
     s = workloads.plain_scale(a.n)
     k, v = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
     st = Streams(k, v)

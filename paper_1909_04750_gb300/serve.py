@@ -11,10 +11,13 @@ Requests (stream id, key, IV, length) arrive over time.  The scheduler loop:
   keystream where the previous one stopped, without re-keying;
 * issues steps over all admitted requests with bits left: sorted by bits
   left and packed 32 per group, every lane of a group produces min(quantum,
-  smallest bits left in the group) bits, so no request runs past its end;
-  the groups with the most work left are clocked one warp per group (the
-  split path: about 7x less time per clock, for the requests that bound the
-  latency);
+  smallest bits left in the group) bits, so no request runs past its end.
+  A stream's bits come out one clock after another, so a request's latency
+  is bound by its length times the time per clock: groups are clocked one
+  warp per group (the split path, several times less time per clock than
+  one thread per group) up to `max_split_groups` (by default 4 warps per SM
+  sub-partition); only the groups with the least work left beyond that run
+  one per thread;
 * writes each step's bytes into a step arena (the response chunk of every
   request served by the step), counted against the device-memory budget
   until the step has completed; with `keep_outputs` each request instead
@@ -41,7 +44,7 @@ NO_STREAM = 0xFFFFFFFF
 
 class Server:
     def __init__(self, max_streams: int, budget_bytes: int = 16 << 30, quantum: int = 1 << 15,
-                 split_quantum: int = 1 << 18, split_min_bits: int = 1 << 22,
+                 split_quantum: int = 1 << 17, split_min_bits: int = 0,
                  max_split_groups: int | None = None, max_groups: int = 1 << 16,
                  max_inflight: int = 2, keep_outputs: bool = False, stream=None):
         if quantum % 32 or split_quantum % 32:
@@ -53,7 +56,7 @@ class Server:
         self.quantum, self.split_quantum = quantum, split_quantum
         self.split_min_bits = split_min_bits
         sms = torch.cuda.get_device_properties(self.stream.device).multi_processor_count
-        self.max_split_groups = max_split_groups if max_split_groups is not None else 4 * sms
+        self.max_split_groups = max_split_groups if max_split_groups is not None else 16 * sms
         self.max_inflight, self.keep_outputs = max_inflight, keep_outputs
         self._h = N.check_ptr(self._L.mickey_server_create(
             max_streams, max_groups, ctypes.c_void_p(self.stream.cuda_stream)))
@@ -103,8 +106,9 @@ class Server:
             arena = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.stream.device)
             offs = np.concatenate(([0], np.cumsum(k_lane[:-1] // 8)))
             outs[: order.size] = np.uint64(arena.data_ptr()) + offs.astype(np.uint64)
+        clocks = np.ascontiguousarray(k_g, np.uint32)   # named: must outlive the call
         N.check(self._L.mickey_server_step(self._h, G, ns, slots.ctypes.data, outs.ctypes.data,
-                                           k_g.astype(np.uint32).ctypes.data))
+                                           clocks.ctypes.data))
         act_done[order] += k_lane
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(self.stream)

@@ -121,3 +121,17 @@ def test_changed_key_for_resident_stream_is_rejected():
     finish = srv.run(reqs + [bad], realtime=False)
     assert np.isnan(finish[-1]) and srv.stats["rejected"] == 1
     _check_against_oracle(srv, reqs, finish[:-1])
+
+
+def test_wide_step_many_groups():
+    # 12,000 requests admitted together: more than 256 groups per step, so
+    # the per-group arrays are past numpy's small-block cache and the step
+    # metadata crosses several pages
+    reqs, keyset = workloads.served_trace(seed=11, rate_per_s=1e6, duration_s=0.012,
+                                          p_continue=0.2, lo_log2_bytes=2, hi_log2_bytes=9)
+    assert len(reqs) > 9000
+    srv = _server(keyset.n, quantum=1024, split_quantum=2048, split_min_bits=2048,
+                  max_split_groups=40)
+    finish = srv.run(reqs, realtime=False)
+    assert srv.stats["completed"] == len(reqs)
+    _check_against_oracle(srv, reqs, finish)
