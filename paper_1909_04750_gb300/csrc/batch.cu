@@ -172,7 +172,7 @@ __device__ __forceinline__ void store_row(uint8_t *o, uint64_t bits, uint32_t t,
 // clock comes first, and put in memory byte order.
 __device__ __forceinline__ void split_group(const uint32_t *state, size_t P, uint32_t g,
                                             uint64_t clocks, uint8_t *row, uint64_t bits,
-                                            uint32_t lane, uint32_t *zbuf) {
+                                            uint32_t lane, uint32_t *zbuf0, uint32_t *zbuf1) {
   SplitLane k;
   split_lane_init(lane, k);
   uint32_t r[4], s[4];
@@ -180,17 +180,18 @@ __device__ __forceinline__ void split_group(const uint32_t *state, size_t P, uin
   for (int q = 0; q < 4; ++q) {
     const int i = int(4 * lane) + q;
     r[q] = i < kReg ? state[size_t(i) * P + g] : 0u;
-    s[q] = i < kReg ? state[size_t(kReg + i) * P + g] : 0u;
+    const int is = split_s_bit(int(lane), q);
+    s[q] = is >= 0 && is < kReg ? state[size_t(kReg + is) * P + g] : 0u;
   }
   const uint32_t full = uint32_t(clocks >> 5);
 #pragma unroll 1
   for (uint32_t t = 0; t < full; ++t) {
-    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, 32);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf0, zbuf1, 32);
     store_row(row, bits, t, __byte_perm(__brev(mine), 0u, 0x0123));
   }
   const int rem = int(clocks & 31);
   if (rem) {
-    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, rem);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf0, zbuf1, rem);
     store_row(row, bits, full, __byte_perm(__brev(mine), 0u, 0x0123));
   }
   __syncwarp();
@@ -211,10 +212,11 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
     if (item < a.n_split) {
-      // the warp's own 32 columns of row 0 of the tile buffer
+      // the warp's own 32 columns of rows 0 and 1 of the tile buffer
       const uint64_t slot = uint64_t(item) * 32 + lane;
+      uint32_t *zb = zs + (threadIdx.x & ~31u);
       split_group(a.state, a.Gpad, item, a.group_bits[item], out + a.slot_off[slot],
-                  a.slot_bits[slot], lane, zs + (threadIdx.x & ~31u));
+                  a.slot_bits[slot], lane, zb, zb + kBatchThreads);
       continue;
     }
     const uint32_t g = a.n_split + (item - a.n_split) * 32 + lane;

@@ -170,10 +170,10 @@ __device__ __forceinline__ void serve_group(const ServeArgs &a, uint32_t g, uint
   scatter_thread(a, g, r, s);
 }
 
-// Split path: lane l brings its stream's row; 200 ballots give lane j the
-// bitsliced words of its register bits 4j..4j+3.
+// Split path: lane l brings its stream's row; 200 ballots give each lane
+// the bitsliced words of its slots (R bit 4j+q, S bit 100-4j-q).
 __device__ __forceinline__ void serve_split(const ServeArgs &a, uint32_t g, uint32_t lane,
-                                            uint32_t *zbuf) {
+                                            uint32_t *zbuf0, uint32_t *zbuf1) {
   const uint32_t st = a.slot_stream[uint64_t(g) * 32 + lane];
   uint32_t row[8];
 #pragma unroll
@@ -183,10 +183,8 @@ __device__ __forceinline__ void serve_split(const ServeArgs &a, uint32_t g, uint
   for (int i = 0; i < kReg; ++i) {
     const uint32_t wr = __ballot_sync(0xffffffffu, (row[i >> 5] >> (31 - (i & 31))) & 1u);
     const uint32_t ws = __ballot_sync(0xffffffffu, (row[4 + (i >> 5)] >> (31 - (i & 31))) & 1u);
-    if (lane == uint32_t(i >> 2)) {
-      r[i & 3] = wr;
-      s[i & 3] = ws;
-    }
+    if (lane == uint32_t(i >> 2)) r[i & 3] = wr;
+    if (lane == uint32_t((100 - i) >> 2)) s[(100 - i) & 3] = ws;
   }
   SplitLane k;
   split_lane_init(lane, k);
@@ -195,20 +193,20 @@ __device__ __forceinline__ void serve_split(const ServeArgs &a, uint32_t g, uint
   const uint32_t full = clocks >> 5;
 #pragma unroll 1
   for (uint32_t t = 0; t < full; ++t) {
-    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, 32);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf0, zbuf1, 32);
     store_lane(base, t, 32, __byte_perm(__brev(mine), 0u, 0x0123));
   }
   const int rem = int(clocks & 31);
   if (rem) {
-    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf, rem);
+    const uint32_t mine = split_tile<kSplitUnroll>(r, s, k, lane, zbuf0, zbuf1, rem);
     store_lane(base, full, rem, __byte_perm(__brev(mine), 0u, 0x0123));
   }
-  // back to rows: word of bit i is held by lane i/4
+  // back to rows
   uint32_t out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int i = 0; i < kReg; ++i) {
     const uint32_t xr = __shfl_sync(0xffffffffu, r[i & 3], i >> 2);
-    const uint32_t xs = __shfl_sync(0xffffffffu, s[i & 3], i >> 2);
+    const uint32_t xs = __shfl_sync(0xffffffffu, s[(100 - i) & 3], (100 - i) >> 2);
     out[i >> 5] |= ((xr >> lane) & 1u) << (31 - (i & 31));
     out[4 + (i >> 5)] |= ((xs >> lane) & 1u) << (31 - (i & 31));
   }
@@ -241,7 +239,7 @@ __global__ void __launch_bounds__(kServeThreads) serve_step_kernel(ServeArgs a) 
 constexpr int kSplitMinBlocksPerSm = 4;
 __global__ void __launch_bounds__(kServeThreads, kSplitMinBlocksPerSm)
     serve_split_kernel(ServeArgs a) {
-  __shared__ uint32_t zs[kServeThreads];   // 32 words per warp
+  __shared__ uint32_t zs[2 * kServeThreads];   // 2 x 32 words per warp
   const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll 1
   for (;;) {
@@ -249,7 +247,8 @@ __global__ void __launch_bounds__(kServeThreads, kSplitMinBlocksPerSm)
     if (lane == 0) item = atomicAdd(a.queue, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_split) break;
-    serve_split(a, item, lane, zs + (threadIdx.x & ~31u));
+    uint32_t *zb = zs + (threadIdx.x & ~31u);
+    serve_split(a, item, lane, zb, zb + kServeThreads);
   }
 }
 
