@@ -31,8 +31,8 @@ namespace mickey {
 // through a 5-stage xor-shuffle butterfly that transposes the 32 x 32 bit
 // tile, so lane l holds its instance's 32 bits.
 
-// clocks per iteration of the split path's tile loop
-constexpr int kSplitUnroll = 8;
+// clocks per iteration of the split path's tile loop (the whole tile)
+constexpr int kSplitUnroll = 32;
 // S bit held by slot q of lane j (R bit: 4j + q)
 __host__ __device__ constexpr int split_s_bit(int j, int q) { return 100 - 4 * j - q; }
 

@@ -10,6 +10,11 @@ stream in ``layout``.  The launch configuration comes from the environment
 
 ``split``: a batch of n streams of ``n_bits`` each whose groups all take the
 one-warp-per-group path (split threshold 1 clock), run ``--reps`` times.
+
+``serve``: a server holding n streams serves one request of ``n_bits`` bits
+per stream ``--reps`` times, each in one step of split groups only (the
+split kernel launches one warp per group, so its counters come from the
+working warps alone).
 """
 import argparse
 
@@ -26,9 +31,21 @@ def main():
     p.add_argument("--n-bits", type=int, default=2048)
     p.add_argument("--layout", default="bytes")
     p.add_argument("--reps", type=int, default=2)
-    p.add_argument("--case", choices=("plain", "split"), default="plain")
+    p.add_argument("--case", choices=("plain", "split", "serve"), default="plain")
     a = p.parse_args()
     build()
+    if a.case == "serve":
+        from .serve import Server
+        s = workloads.plain_scale(a.n)
+        srv = Server(a.n, split_quantum=a.n_bits, split_min_bits=0)
+        reqs = [workloads.Request(0.0, i, s.keys[i].tobytes(), s.ivs[i].tobytes(), 80,
+                                  a.n_bits // 8) for i in range(a.n)]
+        for _ in range(a.reps):
+            srv.run(reqs, realtime=False)
+        torch.cuda.synchronize()
+        srv.free()
+        print("ok", vars(a))
+        return
     if a.case == "split":
         import numpy as np
         from .batch import Batch
