@@ -31,6 +31,22 @@ __device__ __forceinline__ uint32_t s_feedback(uint32_t fb, uint32_t f0,
     return 0u;
 }
 
+// d = f(a, b, c) for the truth table LUT (bit 4a + 2b + c of LUT), as one
+// three-input logic instruction.  Written out so that every register bit
+// of the clock below is exactly the one or two instructions it needs.
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+
+// Truth table of a ^ ((b ^ C0) & (c ^ C1)) for constant C0, C1 (all-ones or
+// zero): the S update of one bit from s_{i-1}, s_i, s_{i+1}.
+__host__ __device__ constexpr uint32_t s_lut(bool c0, bool c1) {
+  return (0xF0u ^ ((0xCCu ^ (c0 ? 0xFFu : 0u)) & (0xAAu ^ (c1 ? 0xFFu : 0u)))) & 0xFFu;
+}
+
 // One bitsliced CLOCK_KG for 32 lanes.
 //   MIX   mixing mode (key/IV loading and preclocks): the R input takes
 //         in ^ s50, both feedbacks take `in` (bit l = input bit of lane l).
@@ -42,7 +58,9 @@ __device__ __forceinline__ uint32_t s_feedback(uint32_t fb, uint32_t f0,
 //         so AND-ing `act` into the non-linear term of exactly those
 //         positions keeps inactive lanes at zero.
 // Both registers are clocked from the old state (control bits
-// CONTROL_BIT_R = s34 ^ r67, CONTROL_BIT_S = s67 ^ r33).
+// CONTROL_BIT_R = s34 ^ r67, CONTROL_BIT_S = s67 ^ r33).  Instruction
+// count: one per bit of R and of S, one more where feedback enters, and
+// CBR, FB&~CBS, FB&CBS (CBS folded into the last two).
 template <bool MIX, bool MASK>
 __device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
                                          uint32_t (&s)[kReg], uint32_t in,
@@ -51,19 +69,18 @@ __device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
   uint32_t fbr = r[99];
   uint32_t fbs = s[99];
   if constexpr (MIX) {
-    fbr = fbr ^ in ^ s[50];
+    fbr = lop3<0x96>(fbr, in, s[50]);
     fbs = fbs ^ in;
   }
-  const uint32_t cbs = s[67] ^ r[33];
-  const uint32_t f0 = fbs & ~cbs;
-  const uint32_t f1 = fbs & cbs;
+  const uint32_t f0 = lop3<0x90>(fbs, s[67], r[33]);   // fbs & ~(s67 ^ r33)
+  const uint32_t f1 = lop3<0x60>(fbs, s[67], r[33]);   // fbs &  (s67 ^ r33)
 
   uint32_t nr[kReg], ns[kReg];
   // CLOCK_R: r'_i = r_{i-1} ^ (cbr & r_i) ^ (i in RTAPS ? fb : 0), r_{-1} = 0
-  nr[0] = (cbr & r[0]) ^ fbr;
+  nr[0] = lop3<0x6A>(cbr, r[0], fbr);                  // (cbr & r0) ^ fb
   static_for<1, kReg>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    uint32_t v = r[i - 1] ^ (cbr & r[i]);
+    uint32_t v = lop3<0x78>(r[i - 1], cbr, r[i]);
     if constexpr (rtap(i)) v ^= fbr;
     nr[i] = v;
   });
@@ -72,11 +89,11 @@ __device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
   ns[0] = fbs;
   static_for<1, kReg - 1>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    constexpr uint32_t c0 = comp0(i) ? ~0u : 0u;
-    constexpr uint32_t c1 = comp1(i) ? ~0u : 0u;
-    uint32_t nl = (s[i] ^ c0) & (s[i + 1] ^ c1);
-    if constexpr (MASK && comp0(i) && comp1(i)) nl &= act;
-    uint32_t v = s[i - 1] ^ nl;
+    uint32_t v;
+    if constexpr (MASK && comp0(i) && comp1(i))
+      v = s[i - 1] ^ lop3<0x02>(s[i], s[i + 1], act);  // ~s_i & ~s_{i+1} & act
+    else
+      v = lop3<s_lut(comp0(i), comp1(i))>(s[i - 1], s[i], s[i + 1]);
     if constexpr (fb0(i) || fb1(i)) v ^= s_feedback<i>(fbs, f0, f1);
     ns[i] = v;
   });
