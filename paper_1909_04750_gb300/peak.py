@@ -9,6 +9,18 @@ from .build import build
 
 CONFIGS = [(1, 128, 20000), (2, 128, 20000), (4, 256, 10000), (8, 256, 5000), (2, 1024, 5000)]
 
+# The integer-logic roofline: GB300 runs 64 three-input LOP3 per SM per
+# clock (half the lanes per cycle; measured with the probe below, every
+# configuration), 152 SMs, 2070 MHz maximum SM clock.
+N_SM = 152
+LOP3_PER_SM_CLK = 64.0
+SM_MAX_MHZ = 2070.0
+
+
+def lop3_peak_tops(n_sm: int = N_SM) -> float:
+    """LOP3 roofline in 10^12 logic ops per second."""
+    return n_sm * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+
 
 def main():
     build()

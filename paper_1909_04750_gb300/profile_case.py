@@ -6,7 +6,9 @@
 ``plain``: creates a handle for ``workloads.plain_scale(n)`` (device
 inputs), then ``--reps`` times re-keys it and generates ``n_bits`` per
 stream in ``layout``.  The launch configuration comes from the environment
-(MICKEY_MODE, MICKEY_UNROLL, MICKEY_STAGE) or the library defaults.
+(MICKEY_MODE, MICKEY_UNROLL, MICKEY_STAGE) or the library defaults, or with
+``--autotune`` from the autotuner (as the benchmarks do; its trial launches
+come first).
 
 ``split``: a batch of n streams of ``n_bits`` each whose groups all take the
 one-warp-per-group path (split threshold 1 clock), run ``--reps`` times.
@@ -32,6 +34,7 @@ def main():
     p.add_argument("--layout", default="bytes")
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--case", choices=("plain", "split", "serve"), default="plain")
+    p.add_argument("--autotune", action="store_true")
     a = p.parse_args()
     build()
     if a.case == "serve":
@@ -62,6 +65,10 @@ def main():
     s = workloads.plain_scale(a.n)
     k, v = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
     st = Streams(k, v)
+    if a.autotune:
+        from . import autotune
+        from .streams import layout_id
+        print("launch:", autotune.describe(autotune.tune(st, a.n_bits, layout_id(a.layout))))
     for _ in range(a.reps):
         st.reset(k, v)
         st.generate(a.n_bits, a.layout)
