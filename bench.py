@@ -36,6 +36,15 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 LOP3_PER_SM_CLK = 64.0
 
+# DRAM traffic of one keystream launch of the plain workload at scale
+# (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu capture of the
+# full-size launch in the autotuned configuration: 79.9 MB read + 2.18 GB
+# written; algorithmic 2.20 GB = 2 GiB of output + the 26.2 MB state read
+# and written).  It stands for the kernel sources it was measured on (their
+# digest) and that launch configuration only; otherwise traffic is null.
+KEYSTREAM_TRAFFIC = {"digest": "b3920bee4ee51723", "launch": "persistent, 4 clocks/step, staged rows",
+                     "bytes_per_launch": 2.26e9}
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -175,7 +184,7 @@ def main():
 
     from paper_1909_04750_gb300 import _native as N
     from paper_1909_04750_gb300 import autotune, workloads
-    from paper_1909_04750_gb300.build import build
+    from paper_1909_04750_gb300.build import build, sources_digest
     from paper_1909_04750_gb300.streams import Streams, ops_per_clock
 
     torch.cuda.set_device(local)
@@ -258,6 +267,12 @@ def main():
     peak = N_SM * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     init_ops = groups * 260 * ops_per_clock(True)
     whole_ops = ops + init_ops
+    alg_bytes = n * n_bits // 8 + 2 * groups * 200 * 4        # output + state in and out
+    traffic = None
+    if (sources_digest() == KEYSTREAM_TRAFFIC["digest"]
+            and autotune.describe(tuned) == KEYSTREAM_TRAFFIC["launch"]
+            and (n, n_bits) == (1 << 20, 1 << 14)):
+        traffic = KEYSTREAM_TRAFFIC["bytes_per_launch"]
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -306,7 +321,8 @@ def main():
                                     / peak,
             "bitsliced_u32_gbit_s": bs_value,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_unit": "bytes per launch", "algorithmic_bytes": alg_bytes,
                          "kernel": "keystream kernel, bytes layout (%s)" % autotune.describe(tuned),
                          "ops_per_clock_per_group": ops_per_clock(False),
                          "peak_basis": "%d SMs x %g LOP3/SM/clk (mickey_probe_lop3) x %g MHz"

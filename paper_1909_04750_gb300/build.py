@@ -7,6 +7,7 @@ Run as ``python -m paper_1909_04750_gb300.build`` or call ``build()``.
 from __future__ import annotations
 
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -39,6 +40,17 @@ def _sources():
 def _headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
                   + glob.glob(os.path.join(INCLUDE, "*.h")))
+
+
+def sources_digest(names=("keystream_kernels.cu", "bitslice.cuh", "tables.cuh",
+                          "internal.h")) -> str:
+    """Short digest of kernel sources (to tie a stored profiler figure to
+    the code it was measured on)."""
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(CSRC, n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _newest(paths):
