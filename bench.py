@@ -183,7 +183,7 @@ def main():
     import torch.distributed as dist
 
     from paper_1909_04750_gb300 import _native as N
-    from paper_1909_04750_gb300 import autotune, workloads
+    from paper_1909_04750_gb300 import autotune, shard, workloads
     from paper_1909_04750_gb300.build import build, sources_digest
     from paper_1909_04750_gb300.streams import Streams, ops_per_clock
 
@@ -193,8 +193,7 @@ def main():
     build()
     n, n_bits = args.n, args.n_bits
     # weak scaling: rank r runs its own 2^20 instances (draws offset by rank)
-    s = workloads.fixed_streams("plain_scale", 2, n * world, n_bits)
-    s = s.subset(np.arange(rank * n, (rank + 1) * n))
+    s = shard.plain_shard(rank, world, n, n_bits)
     keys = torch.from_numpy(s.keys).cuda()
     ivs = torch.from_numpy(s.ivs).cuda()
     lens = torch.from_numpy(s.iv_lens.astype(np.int32)).cuda()
@@ -218,8 +217,7 @@ def main():
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     sampler.start()
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)                           # evict L2 between steps
@@ -229,17 +227,12 @@ def main():
         st.generate(n_bits, "bytes", out=out)           # keystream + transpose kernel
         ev[k][2].record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     clocks = sampler.stop()
     st.sync()
     step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
     ks_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(sum(step_ms))
     bits_per_step = n * n_bits * world
     value = bits_per_step * args.steps / (total_ms * 1e-3) / 1e9
 
@@ -286,18 +279,14 @@ def main():
             h.reset(hk, hv, hl)              # H2D of keys/IVs/lengths + init kernels
             h.generate_host(n_bits, "bytes", out=host_out)   # chunked generate + D2H
         e2e_step()
-        if world > 1:
-            dist.barrier()
+        shard.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": bits_per_step * args.steps / float(tt.item()) / 1e9, "unit": "Gbit/s",
+        dt = shard.max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": bits_per_step * args.steps / dt / 1e9, "unit": "Gbit/s",
                "h2d_bytes_per_step": int(hk.nbytes + hv.nbytes + hl.nbytes) * world,
                "d2h_bytes_per_step": int(host_out.numel()) * world}
         h.free()

@@ -75,8 +75,10 @@ class StreamSet:
 
 
 def fixed_streams(name: str, seed: int, n: int, n_bits: int,
-                  iv_len: int = 80) -> StreamSet:
-    d = splitmix64(seed, 4 * n).reshape(n, 4)
+                  iv_len: int = 80, first: int = 0) -> StreamSet:
+    """Instances first .. first+n-1 of the workload: instance i takes draws
+    4i .. 4i+3 (key low/high, IV low/high)."""
+    d = splitmix64(seed, 4 * n, 4 * first).reshape(n, 4)
     return StreamSet(name, seed, _ten_bytes(d[:, 0], d[:, 1]),
                      _ten_bytes(d[:, 2], d[:, 3]),
                      np.full(n, iv_len, np.uint32), np.full(n, n_bits, np.uint64))
