@@ -9,6 +9,12 @@ run's time -- the work at the plain kernel's measured rate, and the critical
 path (the longest group's clocks at the measured time per clock of a group
 clocked alone by one warp; MICKEY has no jump-ahead, so a stream's bits are
 produced one clock after another).
+
+With --steady K it also runs K batches back to back, round-robin over
+--pipeline handles on their own CUDA streams, so that a batch's groups start
+on the SMs the previous batches' shorter groups have left while their
+longest groups still run: the steady-state rate of a stream of batches,
+which the critical path of a single batch does not bound.
 """
 import argparse
 import json
@@ -60,6 +66,8 @@ def main():
     p.add_argument("--n", type=int, default=workloads.BATCHED["n"])
     p.add_argument("--plain-gbit-s", type=float, default=None,
                    help="plain-workload throughput for the work bound (measured if absent)")
+    p.add_argument("--steady", type=int, default=0, help="batches for the steady-state rate")
+    p.add_argument("--pipeline", type=int, default=4, help="handles (CUDA streams) in flight")
     a = p.parse_args()
     build()
     s = workloads.batched(a.n)
@@ -95,8 +103,39 @@ def main():
     }
     if a.plain_gbit_s:
         line["work_bound_ms"] = bits / (a.plain_gbit_s * 1e9) * 1e3
+    if a.steady:
+        line["steady"] = steady_state(b, s, keys, ivs, tuned, a.steady, a.pipeline)
     print(json.dumps(line), flush=True)
     b.free()
+
+
+def steady_state(b0, s, keys, ivs, tuned, k: int, pipeline: int) -> dict:
+    """K batches back to back over `pipeline` handles on their own streams."""
+    streams = [torch.cuda.Stream() for _ in range(pipeline)]
+    hs = [Batch(s.n_bits, s.iv_lens, stream=st) for st in streams]
+    outs = [torch.empty(b0.output_bytes, dtype=torch.uint8, device="cuda") for _ in hs]
+    for h, o in zip(hs, outs):
+        h.set_config(tuned["unroll"], tuned["blocks_per_sm"], tuned["split_clocks"])
+        h.run(keys, ivs, o)                              # capture + warm-up
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for st in streams:
+        st.wait_event(start)
+    done = []
+    for j in range(k):
+        h = hs[j % pipeline]
+        h.run(keys, ivs, outs[j % pipeline])
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(h.stream)
+        done.append(ev)
+    torch.cuda.synchronize()
+    ms = max(start.elapsed_time(e) for e in done)
+    for h in hs:
+        h.free()
+    bits = int(s.n_bits.sum()) * k
+    return {"batches": k, "pipeline": pipeline, "ms": ms, "ms_per_batch": ms / k,
+            "gbit_s": bits / (ms * 1e-3) / 1e9}
 
 
 if __name__ == "__main__":

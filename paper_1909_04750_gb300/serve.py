@@ -107,13 +107,15 @@ class Server:
             offs = np.concatenate(([0], np.cumsum(k_lane[:-1] // 8)))
             outs[: order.size] = np.uint64(arena.data_ptr()) + offs.astype(np.uint64)
         clocks = np.ascontiguousarray(k_g, np.uint32)   # named: must outlive the call
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev0.record(self.stream)
         N.check(self._L.mickey_server_step(self._h, G, ns, slots.ctypes.data, outs.ctypes.data,
                                            clocks.ctypes.data))
         act_done[order] += k_lane
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(self.stream)
         self.steps += 1
-        return ev, arena, int(k_lane.sum())
+        return ev0, ev, arena, int(k_lane.sum())
 
     # ------------------------------------------------------------------ main loop
     def run(self, requests, realtime: bool = True):
@@ -145,12 +147,15 @@ class Server:
         t_start = time.perf_counter()
         nxt = 0
 
+        busy_ms = 0.0                     # device time spent in steps
+
         def retire(block: bool):
-            nonlocal used
-            while inflight and (block or inflight[0][0].query()):
-                ev, fin, nb = inflight.popleft()
+            nonlocal used, busy_ms
+            while inflight and (block or inflight[0][1].query()):
+                ev0, ev, fin, nb = inflight.popleft()
                 ev.synchronize()
                 finish[fin] = t0.elapsed_time(ev)
+                busy_ms += ev0.elapsed_time(ev)
                 used -= nb
                 block = False
 
@@ -219,11 +224,12 @@ class Server:
                 act_done = np.concatenate((act_done, np.zeros(len(adm), np.int64)))
                 act_buf = np.concatenate((act_buf, np.array(adm_buf, np.uint64)))
             if act_job.size:
-                ev, arena, b = self._issue(act_stream, act_done, bits[act_job], act_buf, reserve)
+                ev0, ev, arena, b = self._issue(act_stream, act_done, bits[act_job], act_buf,
+                                                reserve)
                 served += b
                 done = act_done == bits[act_job]
                 fin = act_job[done]
-                inflight.append((ev, fin, int(bits[fin].sum()) // 8 if arena is None
+                inflight.append((ev0, ev, fin, int(bits[fin].sum()) // 8 if arena is None
                                  else arena.numel()))
                 for sid in act_stream[done]:
                     busy[sid] = False
@@ -238,6 +244,7 @@ class Server:
             elif nxt < n:
                 time.sleep(max(0.0, min(0.005, arrival[nxt] - now)))
         torch.cuda.synchronize()
+        retire(block=True)
         ok = ~rejected & ~np.isnan(finish)
         lat = finish[ok] - release[ok]       # from hand-over to the last byte
         end_ms = float(np.nanmax(finish)) if ok.any() else 0.0
@@ -245,6 +252,8 @@ class Server:
             "requests": n, "completed": int(ok.sum()), "rejected": int(rejected.sum()),
             "steps": self.steps, "served_bits": served, "wall_ms": end_ms,
             "gbit_s": served / (end_ms * 1e-3) / 1e9 if end_ms > 0 else 0.0,
+            "busy_ms": busy_ms,
+            "busy_gbit_s": served / (busy_ms * 1e-3) / 1e9 if busy_ms > 0 else 0.0,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "mean_ms": float(lat.mean()) if lat.size else None,

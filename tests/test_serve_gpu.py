@@ -135,3 +135,33 @@ def test_wide_step_many_groups():
     finish = srv.run(reqs, realtime=False)
     assert srv.stats["completed"] == len(reqs)
     _check_against_oracle(srv, reqs, finish)
+
+
+def test_served_trace_real_lengths_sampled():
+    # the served workload's own length mix (1 KiB .. 64 MiB, 70 % continuing
+    # streams), its first 50 ms of arrivals, through the default server
+    # configuration; every request of the streams the oracle can replay
+    # quickly is compared in full, and the first 64 KiB of the longest
+    # streams' first requests
+    from paper_1909_04750_gb300.serve import Server
+    reqs, keyset = workloads.served_trace(seed=4, duration_s=0.05)
+    srv = Server(keyset.n, budget_bytes=16 << 30, keep_outputs=True)
+    finish = srv.run(reqs, realtime=False)
+    assert srv.stats["completed"] == len(reqs)
+    per = _per_stream(reqs, finish)
+    tot = {sid: sum(8 * reqs[j].n_bytes for j in js) for sid, js in per.items()}
+    short = sorted(sid for sid in per if tot[sid] <= 8_000_000)
+    assert len(short) >= 32
+    first = [reqs[per[sid][0]] for sid in short]
+    ref = oracle.batch_bytes(np.frombuffer(b"".join(r.key for r in first), np.uint8),
+                             np.frombuffer(b"".join(r.iv for r in first), np.uint8), 80,
+                             np.array([tot[sid] for sid in short], np.uint64),
+                             threads=os.cpu_count() or 4)
+    for k, sid in enumerate(short):
+        got = b"".join(srv.outputs[j].cpu().numpy().tobytes() for j in per[sid])
+        assert got == ref[k].tobytes(), sid
+    longest = sorted(per, key=lambda sid: -tot[sid])[:6]
+    for sid in longest:
+        r = reqs[per[sid][0]]
+        head = srv.outputs[per[sid][0]][:65536].cpu().numpy().tobytes()
+        assert head == oracle.stream(r.key, r.iv, 80, 8 * len(head)), sid
