@@ -44,12 +44,15 @@ def _headers():
 
 def sources_digest(names=("keystream_kernels.cu", "bitslice.cuh", "tables.cuh",
                           "internal.h")) -> str:
-    """Short digest of kernel sources (to tie a stored profiler figure to
-    the code it was measured on)."""
+    """Short digest of kernel sources without their // comments and blank
+    lines (to tie a stored profiler figure to the code it was measured on)."""
     h = hashlib.sha256()
     for n in names:
-        with open(os.path.join(CSRC, n), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(CSRC, n)) as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

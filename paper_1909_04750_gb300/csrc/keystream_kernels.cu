@@ -259,16 +259,6 @@ __device__ __forceinline__ void store_release(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Persistent mode: one warp per SM sub-partition, launched cooperatively
-// (all warps resident).  The work line -- warp-group w (32 groups) x tile t,
-// W x NT tiles in all -- is cut into equal segments, one per warp, so every
-// sub-partition gets the same work even when W is not a multiple of the
-// warp count.  A segment holds at most one piece of the warp-group it
-// starts in (a tail: tiles ta..NT) and one of the group it ends in (a head:
-// tiles 0..tb).  A warp runs its head piece first and publishes the state,
-// then its whole groups, then its tail piece, which continues from the
-// state the previous segment's head published (bounded acquire-spin; on
-// timeout the error flag is raised and the piece is skipped).
 // Piece k (in processing order) of the work-line segment of warp `slot`:
 // warp-group w, tiles [ta, tb).  Returns false past the last piece.  The
 // order is: the head of the last warp-group (if the segment ends inside it),
