@@ -10,10 +10,12 @@
 //
 // Run (device, captured once as a CUDA graph and replayed): key/IV loading
 // through the sorting permutation, preclock, then one persistent keystream
-// kernel whose warps take work items -- 32 consecutive groups, i.e. one group
-// per thread -- from an atomic counter.  Items are numbered longest first,
-// so the longest groups start first (longest-processing-time order) and the
-// short ones fill in behind them.
+// kernel whose warps take work items from an atomic counter.  The first
+// n_split items are the longest groups, one per warp (split path: the warp
+// clocks one group, several times less time per clock, for the groups that
+// bound the run); the rest are 32 consecutive groups, one per thread.  Items
+// are numbered longest first, so the longest groups start first
+// (longest-processing-time order) and the short ones fill in behind them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
