@@ -90,3 +90,58 @@ def test_invalid_arguments_rejected_on_host(L):
     L.mickey_free(None)
     assert L.mickey_error_string(N.E_LIMIT) == b"more than 2^40 keystream bits for one key/IV"
     assert L.mickey_version().startswith(b"mickey-gb300")
+
+
+def _plan_only(**kw):
+    # the scheduler's planning step is host logic: build the object without
+    # a device (no handle), with the attributes _plan reads
+    from paper_1909_04750_gb300.serve import Server
+    srv = Server.__new__(Server)
+    srv.quantum, srv.split_quantum = kw.get("quantum", 256), kw.get("split_quantum", 1024)
+    srv.split_min_bits = kw.get("split_min_bits", 0)
+    srv.max_split_groups = kw.get("max_split_groups", 1 << 20)
+    srv.max_groups = kw.get("max_groups", 1 << 16)
+    return srv
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 1000])
+def test_server_plan_groups_never_overrun(n):
+    rng = np.random.default_rng(n)
+    rem = (rng.integers(1, 5000, n) * 8).astype(np.int64)
+    srv = _plan_only(split_min_bits=8 * 3000, max_split_groups=5)
+    order, k_g, ns = srv._plan(rem)
+    G = k_g.size
+    assert G == (n + 31) // 32 and sorted(order.tolist()) == list(range(n))
+    # longest first, every lane of a group gets the same clocks, never more
+    # than its remaining bits, and at most the group's quantum
+    assert np.all(np.diff(rem[order]) <= 0)
+    for g in range(G):
+        lanes = rem[order[32 * g:32 * g + 32]]
+        assert k_g[g] == min(1024 if g < ns else 256, lanes.min())
+    assert ns == min(5, (int((rem >= 8 * 3000).sum()) + 31) // 32)
+
+
+def test_server_plan_caps_groups_and_splits_all_by_default():
+    rem = np.full(100, 4096, np.int64)
+    order, k_g, ns = _plan_only(max_groups=2)._plan(rem)
+    assert k_g.size == 2 and order.size == 64 and ns == 2      # split_min_bits 0: all split
+    assert np.all(k_g == 1024)
+
+
+def test_served_trace_shape():
+    from paper_1909_04750_gb300 import workloads
+    reqs, keys = workloads.served_trace(seed=4, duration_s=2.0)
+    arr = np.array([r.arrival_s for r in reqs])
+    assert np.all(np.diff(arr) >= 0) and arr[-1] < 2.0
+    assert abs(len(reqs) / 2.0 - 1e4) < 500                    # Poisson 10^4/s
+    ids = np.array([r.stream_id for r in reqs])
+    new = np.r_[True, ids[1:] > np.maximum.accumulate(ids)[:-1]]
+    assert abs(1 - new.mean() - 0.7) < 0.02                     # 70 % continue
+    nb = np.array([r.n_bytes for r in reqs])
+    assert nb.min() >= 1024 and nb.max() <= 1 << 26
+    # log-uniform: median near 2^18 bytes
+    assert 2 ** 17.5 < np.median(nb) < 2 ** 18.5
+    # a stream's key/IV never changes
+    seen = {}
+    for r in reqs:
+        assert seen.setdefault(r.stream_id, (r.key, r.iv)) == (r.key, r.iv)
