@@ -168,6 +168,8 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
  *           MICKEY_MODE_PERSISTENT: one warp per SM sub-partition, the
  *           groups x tiles work line cut into equal segments (used only when
  *           there are at least as many 1024-instance warp-groups as warps);
+ *           MICKEY_MODE_PERSISTENT2: the same with two warps per SM
+ *           sub-partition (two blocks per SM, rows staged four tiles deep);
  *           MICKEY_MODE_AUTO: persistent when the grid launch would leave
  *           much of its last wave empty.
  *   unroll  clocks per inner step, 2 or 4.
@@ -177,6 +179,7 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
 #define MICKEY_MODE_AUTO 0
 #define MICKEY_MODE_GRID 1
 #define MICKEY_MODE_PERSISTENT 2
+#define MICKEY_MODE_PERSISTENT2 3
 
 typedef struct {
   int mode, unroll, stage;

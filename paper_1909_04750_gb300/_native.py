@@ -17,7 +17,7 @@ OK = 0
 E_ARG, E_IVLEN, E_LIMIT, E_LAYOUT, E_OOM, E_CUDA, E_TIMEOUT, E_STATE = range(-1, -9, -1)
 LAYOUT_BITSLICED_U32, LAYOUT_BYTES, LAYOUT_U32, LAYOUT_U32_F32 = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE = 0, 1
-MODE_AUTO, MODE_GRID, MODE_PERSISTENT = 0, 1, 2
+MODE_AUTO, MODE_GRID, MODE_PERSISTENT, MODE_PERSISTENT2 = 0, 1, 2, 3
 
 
 class TuneResult(ctypes.Structure):

@@ -18,7 +18,8 @@ from . import _native as N
 
 CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
                           "tune_cache.json")
-MODE_NAMES = {N.MODE_AUTO: "auto", N.MODE_GRID: "grid", N.MODE_PERSISTENT: "persistent"}
+MODE_NAMES = {N.MODE_AUTO: "auto", N.MODE_GRID: "grid", N.MODE_PERSISTENT: "persistent",
+              N.MODE_PERSISTENT2: "persistent x2"}
 _lock = threading.Lock()
 
 

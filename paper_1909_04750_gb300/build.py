@@ -42,7 +42,9 @@ def _headers():
                   + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def sources_digest(names=("keystream_kernels.cu", "bitslice.cuh", "tables.cuh",
+def sources_digest(names=("keystream_kernels.cu", "keystream_device.cuh",
+                          "keystream_persistent.cuh", "keystream_persistent8.cu",
+                          "keystream_persistent4.cu", "bitslice.cuh", "tables.cuh",
                           "internal.h")) -> str:
     """Short digest of kernel sources without their // comments and blank
     lines (to tie a stored profiler figure to the code it was measured on)."""

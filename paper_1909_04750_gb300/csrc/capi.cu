@@ -80,6 +80,7 @@ int default_mode() {
   const char *v = getenv("MICKEY_MODE");
   if (v && !strcmp(v, "grid")) return MICKEY_MODE_GRID;
   if (v && !strcmp(v, "persistent")) return MICKEY_MODE_PERSISTENT;
+  if (v && !strcmp(v, "persistent2")) return MICKEY_MODE_PERSISTENT2;
   return MICKEY_MODE_AUTO;
 }
 
@@ -225,10 +226,18 @@ int check_generate(const mickey_streams *s, uint64_t n_bits, const void *out, in
 // sub-partition) and the grid launch would leave a large part of its last
 // wave empty (a lone warp per sub-partition runs at ~95 % of the rate of
 // two, so below that the grid launch wins).
+bool is_persistent(int mode) {
+  return mode == MICKEY_MODE_PERSISTENT || mode == MICKEY_MODE_PERSISTENT2;
+}
+
+// Blocks per SM of a persistent launch in `mode`.
+uint32_t persist_per_sm(int mode) { return mode == MICKEY_MODE_PERSISTENT2 ? 2u : 1u; }
+
 bool use_persistent(const mickey_streams *s, int mode) {
-  const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * 4;
+  const uint64_t W = (s->G + 31) / 32;
+  const uint64_t slots = uint64_t(s->persist_blocks) * persist_per_sm(mode) * 4;
   if (mode == MICKEY_MODE_GRID || W < slots) return false;
-  if (mode == MICKEY_MODE_PERSISTENT) return true;
+  if (is_persistent(mode)) return true;
   const double waves = double((s->G + kKsThreads - 1) / kKsThreads) / (2.0 * s->sm_count);
   const double eff = waves / std::ceil(waves);
   return eff < 0.93;
@@ -242,10 +251,12 @@ int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
   const int unroll = c.set ? c.unroll : s->unroll;
   const bool stage = c.set ? c.stage : s->stage;
   if (use_persistent(s, mode)) {
-    const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * 4;
+    const uint32_t per_sm = persist_per_sm(mode);
+    const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * per_sm * 4;
     const uint64_t NT = (bits + 31) / 32;
     PersistArgs pa;
-    pa.blocks = uint32_t(s->persist_blocks);
+    pa.blocks = uint32_t(s->persist_blocks) * per_sm;
+    pa.stage_tiles = per_sm == 2 ? 4u : 8u;
     pa.W = uint32_t(W);
     pa.L = (W * NT + slots - 1) / slots;
     pa.flags = s->d_flags;
@@ -502,7 +513,7 @@ mickey_streams *mickey_import_state(const uint8_t *states, const uint64_t *posit
 int mickey_set_config(mickey_streams *s, int layout, int mode, int unroll, int stage) {
   if (!s) return fail(MICKEY_E_ARG, "handle must not be NULL");
   if (!layout_ok(layout)) return fail(MICKEY_E_LAYOUT, "unknown layout %d", layout);
-  if (mode < MICKEY_MODE_AUTO || mode > MICKEY_MODE_PERSISTENT)
+  if (mode < MICKEY_MODE_AUTO || mode > MICKEY_MODE_PERSISTENT2)
     return fail(MICKEY_E_ARG, "unknown mode %d", mode);
   bool known = false;
   for (int k : kUnrolls) known |= (k == unroll);
@@ -551,12 +562,13 @@ int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout, mickey_tune_resu
   cudaMemcpyAsync(saved, s->d_state, st_sz, cudaMemcpyDeviceToDevice, s->stream);
   const auto keep = s->cfg[layout];
   const bool row = layout != MICKEY_LAYOUT_BITSLICED_U32;
-  const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * 4;
+  const uint64_t W = (s->G + 31) / 32;
   int count = 0;
   float best_ms = 1e30f;
   mickey_streams::LayoutCfg best = keep;
-  for (int mode : {MICKEY_MODE_GRID, MICKEY_MODE_PERSISTENT}) {
-    if (mode == MICKEY_MODE_PERSISTENT && W < slots) continue;
+  for (int mode : {MICKEY_MODE_GRID, MICKEY_MODE_PERSISTENT, MICKEY_MODE_PERSISTENT2}) {
+    if (is_persistent(mode) && W < uint64_t(s->persist_blocks) * persist_per_sm(mode) * 4)
+      continue;
     for (int unroll : kUnrolls) {
       for (int stage = 0; stage <= (row && n_bits % 128 == 0 ? 1 : 0); ++stage) {
         auto &c = s->cfg[layout];

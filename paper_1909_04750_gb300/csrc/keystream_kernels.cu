@@ -11,232 +11,10 @@
 //              word per instance (the un-bitslicing of Sec. IV-A run
 //              backwards), stored as bytes, big-endian u32, or u32 + FP32.
 // Finally the state is written back so the next call continues the streams.
-#include "../../include/mickey.h"
-#include "bitslice.cuh"
-#include "internal.h"
+#include "keystream_device.cuh"
 
 namespace mickey {
 namespace {
-
-struct EmitCtx {
-  uint32_t lane_mask;  // valid lanes of this group (last group may be partial)
-  bool vec_ok;         // 16-byte vector stores allowed (bitsliced layout)
-  bool word_ok;        // 4-byte row stores allowed (bytes layout)
-  bool stage;          // row layouts: stage 4 tiles per row, 16-byte stores
-};
-
-// Shared memory of a keystream block: two tile buffers (32 words per
-// thread each) and, when rows are staged, ST words per row per thread laid
-// out [row][thread][ST].  The grid kernel (two blocks per SM) stages ST = 4
-// tiles (16-byte row stores); the persistent kernel (one block per SM)
-// stages ST = 8 tiles, i.e. whole 32-byte sectors, so that no partially
-// written sector has to be merged in L2 or re-read from DRAM.
-constexpr size_t kTileBufWords = 2 * 32 * kKsThreads;
-constexpr size_t row_stage_words(int st) { return size_t(32) * kKsThreads * st; }
-
-// Store lane l's 32 keystream bits t0..t0+nb-1.  `word` holds z_{t0} in bit
-// 31, except for the bytes layout, where it arrives byte-reversed (z_{t0} in
-// bit 7, i.e. in memory byte order).  `tile` points at row 32g, column t0 of
-// the output; rows are `pitch` bytes apart.
-template <int LAYOUT>
-__device__ __forceinline__ void store_row_word(uint8_t *tile, uint32_t pitch,
-                                               uint64_t f32_off, int l, int nb,
-                                               const EmitCtx &e, uint32_t word) {
-  uint8_t *o = tile + uint64_t(uint32_t(l) * pitch);
-  if constexpr (LAYOUT == MICKEY_LAYOUT_BYTES) {
-    if (nb == 32 && e.word_ok) {
-      *reinterpret_cast<uint32_t *>(o) = word;
-    } else {
-      const int nbytes = (nb + 7) >> 3;
-      for (int b = 0; b < nbytes; ++b) o[b] = uint8_t(word >> (8 * b));
-    }
-  } else {
-    *reinterpret_cast<uint32_t *>(o) = word;
-    if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32)
-      *reinterpret_cast<float *>(o + f32_off) = __uint2float_rn(word >> 8) * 0x1p-24f;
-  }
-}
-
-// One eighth of the emission of a 32-clock tile held in shared memory
-// (column `z`, stride kKsThreads).  Slices must run in order 0..7:
-//   bitsliced  slice j stores words 4j..4j+3 (one 128-bit store);
-//   row-major  slices 0-3 apply the block swaps of size 4, 2, 1 to rows
-//              8j..8j+7 in place; slices 4-7 apply the swaps of size 16 and 8
-//              to rows {k, k+8, k+16, k+24} for k = 2(j-4), 2(j-4)+1 and
-//              store the finished words.  The five swaps commute, so the
-//              result is transpose32() of the tile.
-template <int LAYOUT, int ST>
-__device__ __forceinline__ void emit_slice(uint32_t *z, uint32_t *rb, const KeystreamArgs &a,
-                                           uint32_t g, uint64_t t0, int nb,
-                                           const EmitCtx &e, int j) {
-  if constexpr (LAYOUT == MICKEY_LAYOUT_BITSLICED_U32) {
-    uint32_t *o = static_cast<uint32_t *>(a.out) + size_t(g) * a.n_bits + t0;
-    if (nb == 32 && e.vec_ok) {
-      uint4 v;
-      v.x = z[(4 * j + 0) * kKsThreads] & e.lane_mask;
-      v.y = z[(4 * j + 1) * kKsThreads] & e.lane_mask;
-      v.z = z[(4 * j + 2) * kKsThreads] & e.lane_mask;
-      v.w = z[(4 * j + 3) * kKsThreads] & e.lane_mask;
-      reinterpret_cast<uint4 *>(o)[j] = v;
-    } else {
-      for (int c = 4 * j; c < 4 * j + 4 && c < nb; ++c) o[c] = z[c * kKsThreads] & e.lane_mask;
-    }
-  } else if (j < 4) {
-    uint32_t v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = z[(8 * j + k) * kKsThreads];
-    swap_bits<4>(v[0], v[4]); swap_bits<4>(v[1], v[5]);
-    swap_bits<4>(v[2], v[6]); swap_bits<4>(v[3], v[7]);
-    swap_bits<2>(v[0], v[2]); swap_bits<2>(v[1], v[3]);
-    swap_bits<2>(v[4], v[6]); swap_bits<2>(v[5], v[7]);
-    swap_bits<1>(v[0], v[1]); swap_bits<1>(v[2], v[3]);
-    swap_bits<1>(v[4], v[5]); swap_bits<1>(v[6], v[7]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) z[(8 * j + k) * kKsThreads] = v[k];
-  } else {
-    const uint32_t pitch = LAYOUT == MICKEY_LAYOUT_BYTES ? uint32_t((a.n_bits + 7) >> 3)
-                                                         : uint32_t(a.n_bits >> 3);
-    uint8_t *tile = static_cast<uint8_t *>(a.out) + 32ull * g * pitch + (t0 >> 3);
-    const uint64_t f32_off = uint64_t(pitch) * a.n;  // float block follows
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int k = 2 * (j - 4) + h;
-      uint32_t v[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = z[(k + 8 * q) * kKsThreads];
-      swap_halves(v[0], v[2]);
-      swap_halves(v[1], v[3]);
-      swap_bytes<LAYOUT == MICKEY_LAYOUT_BYTES>(v[0], v[1]);
-      swap_bytes<LAYOUT == MICKEY_LAYOUT_BYTES>(v[2], v[3]);
-      // row k + 8q of the transposed tile is lane 31 - k - 8q
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int l = 31 - k - 8 * q;
-        if (e.stage && nb == 32)
-          rb[l * (kKsThreads * ST) + ((t0 >> 5) & (ST - 1))] = v[q];
-        else if ((e.lane_mask >> l) & 1u)
-          store_row_word<LAYOUT>(tile, pitch, f32_off, l, nb, e, v[q]);
-      }
-    }
-  }
-}
-
-template <int LAYOUT, int ST>
-__device__ __forceinline__ void emit_tile(uint32_t *z, uint32_t *rb, const KeystreamArgs &a,
-                                          uint32_t g, uint64_t t0, int nb, const EmitCtx &e) {
-#pragma unroll 1
-  for (int j = 0; j < 8; ++j) emit_slice<LAYOUT, ST>(z, rb, a, g, t0, nb, e, j);
-}
-
-// Row layouts with staging: write the staged words of tiles tA..tB (one
-// aligned block of ST tiles, or part of one) of every valid row; a whole
-// block goes out as ST/4 16-byte stores per row (and per f32 row).
-template <int LAYOUT, int ST>
-__device__ __forceinline__ void flush_rows(const uint32_t *rb, const KeystreamArgs &a,
-                                           uint32_t g, uint32_t tA, uint32_t tB,
-                                           const EmitCtx &e) {
-  const uint32_t pitch = uint32_t(a.n_bits >> 3);
-  uint8_t *base = static_cast<uint8_t *>(a.out) + 32ull * g * pitch + uint64_t(tA) * 4;
-  const uint64_t f32_off = uint64_t(pitch) * a.n;
-  const int n = int(tB - tA) + 1, j0 = int(tA & (ST - 1));
-#pragma unroll 1
-  for (int l = 0; l < 32; ++l) {
-    if (!((e.lane_mask >> l) & 1u)) continue;
-    const uint32_t *src = rb + l * (kKsThreads * ST);
-    uint8_t *o = base + uint64_t(uint32_t(l) * pitch);
-    if (n == ST) {
-#pragma unroll
-      for (int h = 0; h < ST / 4; ++h) {
-        const uint4 v = reinterpret_cast<const uint4 *>(src)[h];
-        reinterpret_cast<uint4 *>(o)[h] = v;
-        if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32) {
-          float4 f;
-          f.x = __uint2float_rn(v.x >> 8) * 0x1p-24f;
-          f.y = __uint2float_rn(v.y >> 8) * 0x1p-24f;
-          f.z = __uint2float_rn(v.z >> 8) * 0x1p-24f;
-          f.w = __uint2float_rn(v.w >> 8) * 0x1p-24f;
-          reinterpret_cast<float4 *>(o + f32_off)[h] = f;
-        }
-      }
-    } else {
-      for (int j = 0; j < n; ++j) {
-        const uint32_t w = src[j0 + j];
-        reinterpret_cast<uint32_t *>(o)[j] = w;
-        if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32)
-          reinterpret_cast<float *>(o + f32_off)[j] = __uint2float_rn(w >> 8) * 0x1p-24f;
-      }
-    }
-  }
-}
-
-// Keystream bits of tiles [tile_a, tile_b) of group g (tile t covers clocks
-// 32t .. 32t+31 of this call; the last tile may be partial), continuing from
-// and writing back the group's state.  The tile buffer is double-buffered:
-// while the 32 clocks of tile k run (U clocks per step), the eight emission
-// slices of tile k-1 are interleaved with them, so the clock's independent
-// LOP3s hide the latency of the emission's shared-memory and global accesses.
-template <int LAYOUT, int U, int ST>
-__device__ __forceinline__ void run_piece(const KeystreamArgs &a, EmitCtx e, uint32_t g,
-                                          uint32_t *zbuf0, uint32_t *zbuf1, uint32_t *rb,
-                                          uint32_t tile_a, uint32_t tile_b) {
-  static_assert(U == 2 || U == 4, "one emission slice per 4 clocks");
-  const size_t P = a.Gpad;
-  uint32_t r[kReg], s[kReg];
-  const uint32_t *src = a.state + g;
-#pragma unroll
-  for (int i = 0; i < kReg; ++i) {
-    r[i] = src[size_t(i) * P];
-    s[i] = src[size_t(kReg + i) * P];
-  }
-  if (g != a.G - 1) e.lane_mask = ~0u;
-
-  const uint32_t full = uint32_t(a.n_bits >> 5);
-  const uint32_t fend = tile_b < full ? tile_b : full;
-#pragma unroll 1
-  for (uint32_t tile = tile_a; tile < fend; ++tile) {
-    uint32_t *cur = (tile & 1) ? zbuf1 : zbuf0;
-    uint32_t *prev = (tile & 1) ? zbuf0 : zbuf1;
-#pragma unroll 1
-    for (int c = 0; c < 32; c += U) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        cur[(c + u) * kKsThreads] = r[0] ^ s[0];
-        clock_kg<false, false>(r, s, 0u, 0u);
-      }
-      if (tile > tile_a && (c & 3) == 0)
-        emit_slice<LAYOUT, ST>(prev, rb, a, g, uint64_t(tile - 1) << 5, 32, e, c >> 2);
-    }
-    if (LAYOUT != MICKEY_LAYOUT_BITSLICED_U32 && e.stage && tile > tile_a &&
-        ((tile - 1) & (ST - 1)) == ST - 1)
-      flush_rows<LAYOUT, ST>(rb, a, g, max(tile - ST, tile_a), tile - 1, e);
-  }
-  if (fend > tile_a) {
-    emit_tile<LAYOUT, ST>((fend & 1) ? zbuf0 : zbuf1, rb, a, g, uint64_t(fend - 1) << 5, 32, e);
-    if (LAYOUT != MICKEY_LAYOUT_BITSLICED_U32 && e.stage)
-      flush_rows<LAYOUT, ST>(rb, a, g, max((fend - 1) & ~uint32_t(ST - 1), tile_a), fend - 1, e);
-  }
-  if (tile_b > full && (a.n_bits & 31)) {  // the partial last tile
-    uint32_t *cur = (full & 1) ? zbuf1 : zbuf0;
-    const int rem = int(a.n_bits & 31);
-#pragma unroll 1
-    for (int c = 0; c < 32; ++c) {
-      if (c < rem) {
-        cur[c * kKsThreads] = r[0] ^ s[0];
-        clock_kg<false, false>(r, s, 0u, 0u);
-      } else {
-        cur[c * kKsThreads] = 0u;
-      }
-    }
-    emit_tile<LAYOUT, ST>(cur, rb, a, g, uint64_t(full) << 5, rem, e);
-  }
-
-  uint32_t *dst = a.state + g;
-#pragma unroll
-  for (int i = 0; i < kReg; ++i) {
-    dst[size_t(i) * P] = r[i];
-    dst[size_t(kReg + i) * P] = s[i];
-  }
-}
 
 // Grid mode: one thread per group, all tiles.
 template <int LAYOUT, int U>
@@ -250,129 +28,8 @@ __global__ void __launch_bounds__(kKsThreads)
                        uint32_t((a.n_bits + 31) >> 5));
 }
 
-__device__ __forceinline__ uint32_t load_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void store_release(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Piece k (in processing order) of the work-line segment of warp `slot`:
-// warp-group w, tiles [ta, tb).  Returns false past the last piece.  The
-// order is: the head of the last warp-group (if the segment ends inside it),
-// the whole warp-groups, the tail of the first warp-group (if the segment
-// starts inside it).  Recomputed per piece so that only (slot, k) stay live
-// across the clock loop.
-__device__ __forceinline__ bool segment_piece(const PersistArgs &p, uint64_t NT, uint32_t slot,
-                                              uint32_t k, uint32_t &w, uint32_t &ta,
-                                              uint32_t &tb) {
-  const uint64_t total = uint64_t(p.W) * NT;
-  const uint64_t seg_a = uint64_t(slot) * p.L;
-  const uint64_t seg_b = seg_a + p.L < total ? seg_a + p.L : total;
-  if (seg_a >= seg_b) return false;
-  const uint64_t w_first = seg_a / NT, w_last = (seg_b - 1) / NT;
-  const bool has_tail = seg_a > w_first * NT;
-  const bool has_head = (seg_b - w_last * NT) < NT && !(has_tail && w_last == w_first);
-  const uint64_t full_lo = w_first + (has_tail ? 1 : 0);
-  const uint64_t full_end = w_last + 1 - (has_head ? 1 : 0);
-  const uint64_t full_n = full_end > full_lo ? full_end - full_lo : 0;
-  const uint64_t n_pieces = (has_head ? 1 : 0) + full_n + (has_tail ? 1 : 0);
-  if (k >= n_pieces) return false;
-  const uint64_t kk = k - (has_head ? 1 : 0);
-  const uint64_t ww = (has_head && k == 0) ? w_last : (kk < full_n ? full_lo + kk : w_first);
-  w = uint32_t(ww);
-  ta = uint32_t(ww == w_first ? seg_a - ww * NT : 0);
-  tb = uint32_t(ww == w_last ? seg_b - ww * NT : NT);
-  return true;
-}
-
-// Persistent mode: one warp per SM sub-partition, launched cooperatively
-// (all warps resident).  The work line -- warp-group w (32 groups) x tile t,
-// W x NT tiles in all -- is cut into equal segments, one per warp, so every
-// sub-partition gets the same work even when W is not a multiple of the
-// warp count.  A segment holds at most one piece of the warp-group it
-// starts in (a tail: tiles ta..NT) and one of the group it ends in (a head:
-// tiles 0..tb).  A warp runs its head piece first and publishes the state,
-// then its whole groups, then its tail piece, which continues from the
-// state the previous segment's head published (bounded acquire-spin; on
-// timeout the error flag is raised and the piece is skipped).
-template <int LAYOUT, int U>
-__global__ void __launch_bounds__(kKsThreads, 1)
-    keystream_persistent_kernel(KeystreamArgs a, EmitCtx e, PersistArgs p) {
-  extern __shared__ uint32_t zs[];
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t slot = blockIdx.x * (kKsThreads / 32) + (threadIdx.x >> 5);
-  const uint64_t NT = (a.n_bits + 31) >> 5;
-#pragma unroll 1
-  for (uint32_t k = 0;; ++k) {
-    uint32_t w, ta, tb;
-    if (!segment_piece(p, NT, slot, k, w, ta, tb)) break;
-    if (ta > 0) {  // tail: wait for the head piece of this warp-group
-      uint32_t it = 0;
-      bool ok = true;
-      while (load_acquire(p.flags + w) != p.epoch) {
-        if (++it > p.spin_limit) {
-          ok = false;
-          break;
-        }
-        __nanosleep(256);
-      }
-      if (!__all_sync(0xffffffffu, ok)) {
-        if (lane == 0) atomicOr(p.err, kErrTimeout);
-        continue;
-      }
-    }
-    const uint32_t g = w * 32 + lane;
-    if (g < a.G)
-      run_piece<LAYOUT, U, 8>(a, e, g, zs + threadIdx.x, zs + 32 * kKsThreads + threadIdx.x,
-                              zs + kTileBufWords + 8 * threadIdx.x, ta, tb);
-    if (ta == 0 && tb < NT) {  // head: publish the state for the next segment
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) store_release(p.flags + w, p.epoch);
-    }
-  }
-}
-
-size_t smem_bytes(const EmitCtx &e, int st) {
-  return 4 * (kTileBufWords + (e.stage ? row_stage_words(st) : 0));
-}
-
-template <class K>
-cudaError_t allow_smem(K kernel, int st) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(4 * (kTileBufWords + row_stage_words(st))));
-}
-
-template <int LAYOUT, int U>
-cudaError_t launch_persistent(const KeystreamArgs &a, const EmitCtx &e, const PersistArgs &p,
-                              cudaStream_t st) {
-  cudaError_t err = allow_smem(keystream_persistent_kernel<LAYOUT, U>, 8);
-  if (err != cudaSuccess) return err;
-  cudaLaunchConfig_t cfg = {};
-  cfg.dynamicSmemBytes = smem_bytes(e, 8);
-  cfg.gridDim = dim3(p.blocks);
-  cfg.blockDim = dim3(kKsThreads);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, keystream_persistent_kernel<LAYOUT, U>, a, e, p);
-}
-
 template <int LAYOUT>
-cudaError_t launch_layout(const KeystreamArgs &a, int unroll, const EmitCtx &e,
-                          const PersistArgs *p, cudaStream_t st) {
-  if (p) {
-    cudaError_t err = unroll == 2 ? launch_persistent<LAYOUT, 2>(a, e, *p, st)
-                      : unroll == 4 ? launch_persistent<LAYOUT, 4>(a, e, *p, st)
-                                    : cudaErrorInvalidValue;
-    return err != cudaSuccess ? err : cudaGetLastError();
-  }
+cudaError_t launch_grid(const KeystreamArgs &a, int unroll, const EmitCtx &e, cudaStream_t st) {
   const uint32_t blocks = (a.G + kKsThreads - 1) / kKsThreads;
   const size_t smem = smem_bytes(e, 4);
   cudaError_t err = cudaSuccess;
@@ -401,16 +58,21 @@ cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll, boo
   e.vec_ok = (addr % 16 == 0) && (a.n_bits % 4 == 0);
   e.word_ok = (addr % 4 == 0) && (((a.n_bits + 7) / 8) % 4 == 0);
   e.stage = stage && layout != MICKEY_LAYOUT_BITSLICED_U32 && (addr % 16 == 0) &&
-            (a.n_bits % (p ? 256 : 128) == 0);
+            (a.n_bits % (p ? 32 * p->stage_tiles : 128) == 0);
+  if (p) {
+    if (p->stage_tiles == 8) return launch_persistent8(a, layout, unroll, e, *p, st);
+    if (p->stage_tiles == 4) return launch_persistent4(a, layout, unroll, e, *p, st);
+    return cudaErrorInvalidValue;
+  }
   switch (layout) {
     case MICKEY_LAYOUT_BITSLICED_U32:
-      return launch_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, unroll, e, p, st);
+      return launch_grid<MICKEY_LAYOUT_BITSLICED_U32>(a, unroll, e, st);
     case MICKEY_LAYOUT_BYTES:
-      return launch_layout<MICKEY_LAYOUT_BYTES>(a, unroll, e, p, st);
+      return launch_grid<MICKEY_LAYOUT_BYTES>(a, unroll, e, st);
     case MICKEY_LAYOUT_U32:
-      return launch_layout<MICKEY_LAYOUT_U32>(a, unroll, e, p, st);
+      return launch_grid<MICKEY_LAYOUT_U32>(a, unroll, e, st);
     case MICKEY_LAYOUT_U32_F32:
-      return launch_layout<MICKEY_LAYOUT_U32_F32>(a, unroll, e, p, st);
+      return launch_grid<MICKEY_LAYOUT_U32_F32>(a, unroll, e, st);
     default:
       return cudaErrorInvalidValue;
   }

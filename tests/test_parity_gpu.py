@@ -272,18 +272,20 @@ def test_fused_full_size_sampled():
 
 # -------------------------------------------------------------- persistent mode
 
+@pytest.mark.parametrize("mode", ["persistent", "persistent2"])
 @pytest.mark.parametrize("stage", ["0", "1"])
 @pytest.mark.parametrize("n,n_bits,blocks", [(10 * 1024, 1000, 1), (7 * 1024 + 5, 4096, 1),
                                              (41 * 1024 - 3, 776, 2), (20 * 1024, 64, 3),
                                              (10 * 1024, 4096, 3), (41 * 1024 - 3, 1024, 2)])
-def test_persistent_mode_matches_grid_and_oracle(monkeypatch, n, n_bits, blocks, stage):
-    # The work line is cut into 4*blocks equal segments, so warp-groups are
-    # split into head and tail pieces run by different warps.
+def test_persistent_mode_matches_grid_and_oracle(monkeypatch, n, n_bits, blocks, stage, mode):
+    # The work line is cut into 4*blocks (persistent2: 8*blocks) equal
+    # segments, so warp-groups are split into head and tail pieces run by
+    # different warps.
     s = workloads.plain_scale(n)
     monkeypatch.setenv("MICKEY_STAGE", stage)
     monkeypatch.setenv("MICKEY_MODE", "grid")
     st_g = _streams(s)
-    monkeypatch.setenv("MICKEY_MODE", "persistent")
+    monkeypatch.setenv("MICKEY_MODE", mode)
     monkeypatch.setenv("MICKEY_PERSIST_BLOCKS", str(blocks))
     st_p = _streams(s)
     got = {}
