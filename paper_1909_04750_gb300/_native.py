@@ -31,9 +31,14 @@ _lib = None
 c_void_p, c_size_t, c_uint64, c_int, c_char_p = (ctypes.c_void_p, ctypes.c_size_t,
                                                  ctypes.c_uint64, ctypes.c_int,
                                                  ctypes.c_char_p)
+c_uint8 = ctypes.c_uint8
 
 # name: (restype, argtypes)
 SIGNATURES = {
+    "mickey_lfsr_generate": (c_int, [c_void_p, c_size_t, c_int, c_uint64, c_uint64, c_void_p, c_int,
+                                     c_void_p]),
+    "mickey_crc8": (c_int, [c_void_p, c_size_t, c_size_t, c_uint8, c_uint8, c_uint8, c_void_p, c_int,
+                            c_void_p]),
     "mickey_init_streams": (c_void_p, [c_void_p, c_void_p, c_void_p, c_size_t]),
     "mickey_init_streams_ex": (c_void_p, [c_void_p, c_void_p, c_void_p, c_size_t, c_int,
                                           c_void_p]),

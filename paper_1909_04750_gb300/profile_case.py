@@ -13,6 +13,9 @@ come first).
 ``split``: a batch of n streams of ``n_bits`` each whose groups all take the
 one-warp-per-group path (split threshold 1 clock), run ``--reps`` times.
 
+``crc8``: CRC-8 (0x1D, preset and final XOR 0xFF) of n messages of
+``n_bits / 8`` bytes each (random, device-resident), ``--reps`` times.
+
 ``serve``: a server holding n streams serves one request of ``n_bits`` bits
 per stream ``--reps`` times, each in one step of split groups only (the
 split kernel launches one warp per group, so its counters come from the
@@ -33,10 +36,20 @@ def main():
     p.add_argument("--n-bits", type=int, default=2048)
     p.add_argument("--layout", default="bytes")
     p.add_argument("--reps", type=int, default=2)
-    p.add_argument("--case", choices=("plain", "split", "serve"), default="plain")
+    p.add_argument("--case", choices=("plain", "split", "serve", "crc8"), default="plain")
     p.add_argument("--autotune", action="store_true")
     a = p.parse_args()
     build()
+    if a.case == "crc8":
+        from .lfsr import crc8
+        g = torch.Generator(device="cuda").manual_seed(5)
+        data = torch.randint(0, 256, (a.n, a.n_bits // 8), dtype=torch.uint8, device="cuda",
+                             generator=g)
+        for _ in range(a.reps):
+            crc8(data, 0x1D, 0xFF, 0xFF)
+        torch.cuda.synchronize()
+        print("ok", vars(a))
+        return
     if a.case == "serve":
         from .serve import Server
         s = workloads.plain_scale(a.n)

@@ -145,3 +145,19 @@ def test_served_trace_shape():
     seen = {}
     for r in reqs:
         assert seen.setdefault(r.stream_id, (r.key, r.iv)) == (r.key, r.iv)
+
+
+def test_lfsr_and_crc_reject_bad_arguments_on_the_host(L):
+    seeds = np.ones(4, np.uint64)
+    out = np.zeros(16, np.uint32)      # never written: every call below fails first
+    p, o = seeds.ctypes.data, out.ctypes.data
+    assert L.mickey_lfsr_generate(p, 4, 1, 1, 8, o, N.MEM_HOST, None) == N.E_ARG      # degree
+    assert L.mickey_lfsr_generate(p, 4, 65, 1, 8, o, N.MEM_HOST, None) == N.E_ARG
+    assert L.mickey_lfsr_generate(p, 4, 8, 0b10, 8, o, N.MEM_HOST, None) == N.E_ARG   # no a_0
+    assert L.mickey_lfsr_generate(p, 4, 8, 1 << 8, 8, o, N.MEM_HOST, None) == N.E_ARG  # tap >= degree
+    assert L.mickey_lfsr_generate(p, 0, 8, 1, 8, o, N.MEM_HOST, None) == N.E_ARG      # empty
+    assert L.mickey_lfsr_generate(None, 4, 8, 1, 8, o, N.MEM_HOST, None) == N.E_ARG
+    assert L.mickey_crc8(None, 4, 4, 7, 0, 0, o, N.MEM_HOST, None) == N.E_ARG   # data, len > 0
+    assert L.mickey_crc8(p, 4, 4, 7, 0, 0, None, N.MEM_HOST, None) == N.E_ARG   # crc
+    assert L.mickey_crc8(p, 4, 4, 7, 0, 0, o, 5, None) == N.E_ARG                     # mem kind
+    assert L.mickey_crc8(p, 0, 4, 7, 0, 0, o, N.MEM_HOST, None) == N.OK               # nothing to do
