@@ -271,7 +271,11 @@ def main():
     e2e = None
     if not args.no_e2e:
         host_out = torch.empty((n, n_bits // 8), dtype=torch.uint8, pin_memory=True)
-        hk, hv, hl = s.keys, s.ivs, s.iv_lens
+        # the step's inputs live in pinned host memory (copied in every step)
+        pk = torch.from_numpy(s.keys).pin_memory()
+        pv = torch.from_numpy(s.ivs).pin_memory()
+        pl = torch.from_numpy(s.iv_lens.astype(np.uint32).view(np.int32)).pin_memory()
+        hk, hv, hl = pk.numpy(), pv.numpy(), pl.numpy().view(np.uint32)
 
         h = Streams(hk, hv, hl)            # host-memory inputs
 
