@@ -175,6 +175,14 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
  *   unroll  clocks per inner step, 2 or 4.
  *   stage   row layouts: stage four 32-bit words per row in shared memory
  *           and write 16-byte chunks (needs n_bits % 128 == 0).
+ * Environment, read when a handle is created: MICKEY_MODE (grid,
+ * persistent, persistent2), MICKEY_UNROLL (2, 4), MICKEY_STAGE (0, 1) and
+ * MICKEY_PERSIST_BLOCKS (fewer persistent blocks than SMs) set the defaults;
+ * MICKEY_SPIN_LIMIT bounds a persistent tail piece's wait for its head
+ * (polls of about 256 ns, default 2^24), after which the piece is skipped and
+ * mickey_sync reports MICKEY_E_TIMEOUT; MICKEY_TEST_UNPUBLISHED=1 is a test
+ * hook that makes every such wait run out (tails wait for a value no head
+ * writes), to exercise that path without a fault.
  * ------------------------------------------------------------------------ */
 #define MICKEY_MODE_AUTO 0
 #define MICKEY_MODE_GRID 1

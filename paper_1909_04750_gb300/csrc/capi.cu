@@ -37,6 +37,8 @@ struct mickey_streams {
   int persist_blocks = 0;         // blocks of the persistent kernel (<= SMs)
   uint32_t *d_flags = nullptr;    // persistent mode: one word per warp-group
   uint32_t epoch = 0;
+  uint32_t spin_limit = 1u << 24;   // polls of ~256 ns before a tail piece gives up
+  bool test_unpublished = false;    // test hook: tails wait for a value no head writes
   std::vector<uint64_t> pos;
   // device staging for mickey_generate_host
   void *d_stage[2] = {nullptr, nullptr};
@@ -138,6 +140,11 @@ int allocate(mickey_streams *s, size_t n) {
   s->unroll = default_unroll();
   s->mode = default_mode();
   if (const char *v = getenv("MICKEY_STAGE")) s->stage = atoi(v) != 0;
+  if (const char *v = getenv("MICKEY_SPIN_LIMIT")) {
+    const long long l = atoll(v);
+    if (l > 0 && l < (1ll << 31)) s->spin_limit = uint32_t(l);
+  }
+  if (const char *v = getenv("MICKEY_TEST_UNPUBLISHED")) s->test_unpublished = atoi(v) != 0;
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
   CUDA_TRY(cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev),
@@ -260,8 +267,10 @@ int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
     pa.W = uint32_t(W);
     pa.L = (W * NT + slots - 1) / slots;
     pa.flags = s->d_flags;
-    pa.epoch = ++s->epoch;
-    pa.spin_limit = 1u << 24;
+    s->epoch = s->epoch % 0x7fffffffu + 1;   // 1 .. 2^31 - 1 (0 is the flags' initial value)
+    pa.epoch = s->epoch;
+    pa.wait_epoch = s->test_unpublished ? (s->epoch | 0x80000000u) : s->epoch;
+    pa.spin_limit = s->spin_limit;
     pa.err = s->d_err;
     CUDA_TRY(launch_keystream(ka, layout, unroll, stage, &pa, s->stream),
              "keystream_persistent_kernel launch");

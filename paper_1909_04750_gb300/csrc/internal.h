@@ -82,6 +82,8 @@ struct PersistArgs {
   uint64_t L;           // tiles of the work line per warp
   uint32_t *flags;      // W words
   uint32_t epoch;       // value a finished head piece writes
+  uint32_t wait_epoch;  // value a tail piece waits for (== epoch; differs only under the
+                        // MICKEY_TEST_UNPUBLISHED test hook, to make the wait run out)
   uint32_t spin_limit;  // bounded wait of a tail piece (iterations of ~256 ns)
   int *err;
 };

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kKsThreads, 8 / ST)
     if (ta > 0) {  // tail: wait for the head piece of this warp-group
       uint32_t it = 0;
       bool ok = true;
-      while (load_acquire(p.flags + w) != p.epoch) {
+      while (load_acquire(p.flags + w) != p.wait_epoch) {
         if (++it > p.spin_limit) {
           ok = false;
           break;

@@ -326,3 +326,27 @@ def test_autotune_keeps_positions_and_output():
     ref = _ref(s.subset(rows), 1280)
     assert np.array_equal(first[rows], ref[:, :32])
     assert np.array_equal(rest[rows], ref[:, 32:])
+
+
+def test_persistent_wait_runs_out_without_a_fault(monkeypatch):
+    # the hand-off wait of a tail piece is bounded: with the test hook no
+    # head publishes the value the tails wait for, so every tail gives up
+    # after MICKEY_SPIN_LIMIT polls, the call still returns, mickey_sync
+    # reports the timeout, and the context keeps working
+    s = workloads.plain_scale(10 * 1024)
+    monkeypatch.setenv("MICKEY_MODE", "persistent")
+    monkeypatch.setenv("MICKEY_PERSIST_BLOCKS", "1")
+    monkeypatch.setenv("MICKEY_SPIN_LIMIT", "2000")
+    monkeypatch.setenv("MICKEY_TEST_UNPUBLISHED", "1")
+    st = _streams(s)
+    st.generate(1000, "bytes")
+    with pytest.raises(N.MickeyError) as ei:
+        st.sync()
+    assert ei.value.code == N.E_TIMEOUT
+    st.free()
+    monkeypatch.delenv("MICKEY_TEST_UNPUBLISHED")
+    ok = _streams(s)
+    got = ok.generate(1000, "bytes").cpu().numpy()
+    ok.sync()
+    rows = _sample_rows(s.n, 48, 6)
+    assert np.array_equal(got[rows], _ref(s.subset(rows), 1000)[:, :125])
