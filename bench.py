@@ -132,10 +132,17 @@ def cpu_baseline(n_bits: int, seconds: float = 3.0):
         if elapsed >= seconds or count >= (1 << 20):
             break
         count = int(count * max(2.0, 1.2 * seconds / max(elapsed, 1e-3)))
+    # one core: the same oracle on one thread, a smaller sample
+    one = max(8, min(count // cores, 256))
+    s1 = workloads.plain_scale(one)
+    t = time.perf_counter()
+    oracle.batch_bytes(s1.keys, s1.ivs, s1.iv_lens, n_bits, threads=1)
+    one_core = one * n_bits / (time.perf_counter() - t) / 1e9
     return {"value": total_bits / elapsed / 1e9, "unit": "Gbit/s", "cores": cores,
-            "kind": "oracle",
+            "kind": "oracle", "one_core_gbit_s": one_core,
             "sample": "%d instances x %d keystream bits (+260 init clocks each) of the same "
-                      "workload, scalar C oracle, one instance per task" % (count, n_bits)}
+                      "workload, scalar C oracle, one instance per task; one core: %d "
+                      "instances on one thread" % (count, n_bits, one)}
 
 
 def run_reference(args, rank, world):
