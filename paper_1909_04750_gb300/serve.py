@@ -2,10 +2,11 @@
 
 Requests (stream id, key, IV, length) arrive over time.  The scheduler loop:
 
-* admits each arrived request as soon as its stream is free: a stream's
-  requests run one after another in arrival order, and a stream is free
-  again once its previous request's last step has been issued (steps run in
-  order on one CUDA stream, so the state table is always up to date);
+* appends each arrived request to its stream's chain: a stream's requests
+  continue one keystream in arrival order, so the chain is one run of bits
+  and a step may end one request and go on into the next (with per-request
+  output buffers a step stops at request boundaries instead); steps run in
+  order on one CUDA stream, so the state table is always up to date;
 * loads and preclocks streams that appear for the first time; afterwards
   their state stays in the device table, so follow-up requests continue the
   keystream where the previous one stopped, without re-keying;
@@ -89,18 +90,20 @@ class Server:
         k_g = np.minimum(quant, srt[last]).astype(np.int64)
         return order, k_g, min(ns, G)
 
-    def _issue(self, act_stream, act_done, act_bits, act_buf, reserve):
-        rem = act_bits - act_done
+    def _issue(self, act, rem, keep_ptr, reserve):
+        """One step over the active streams `act` with `rem` bits left each
+        (keep_ptr: per-stream output address in keep_outputs mode).  Returns
+        (start event, end event, step arena or None, order, bits per lane)."""
         order, k_g, ns = self._plan(rem)
         G = k_g.size
         k_lane = np.repeat(k_g, 32)[: order.size]
         nbytes = int(k_lane.sum()) // 8
         slots = np.full(32 * G, NO_STREAM, np.uint32)
-        slots[: order.size] = act_stream[order]
+        slots[: order.size] = act[order]
         outs = np.zeros(32 * G, np.uint64)
         arena = None
         if self.keep_outputs:
-            outs[: order.size] = act_buf[order] + (act_done[order] // 8).astype(np.uint64)
+            outs[: order.size] = keep_ptr[order]
         else:
             reserve(nbytes)
             arena = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.stream.device)
@@ -111,11 +114,10 @@ class Server:
         ev0.record(self.stream)
         N.check(self._L.mickey_server_step(self._h, G, ns, slots.ctypes.data, outs.ctypes.data,
                                            clocks.ctypes.data))
-        act_done[order] += k_lane
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(self.stream)
         self.steps += 1
-        return ev0, ev, arena, int(k_lane.sum())
+        return ev0, ev, arena, order, k_lane
 
     # ------------------------------------------------------------------ main loop
     def run(self, requests, realtime: bool = True):
@@ -123,31 +125,32 @@ class Server:
         Returns per-request completion times (ms of device time since the
         start, NaN if rejected); self.stats holds the summary, latency being
         measured from the moment the server saw the request (its arrival
-        time when `realtime`, the start otherwise) to its last step's end."""
+        time when `realtime`, the start otherwise) to the end of the step
+        that produced its last byte."""
         n = len(requests)
         bits = np.array([8 * r.n_bytes for r in requests], np.int64)
         arrival = np.array([r.arrival_s for r in requests], np.float64)
         finish = np.full(n, np.nan)
         release = np.zeros(n)             # ms since the start the server saw the request
         rejected = np.zeros(n, bool)
-        queues: dict = {}                 # stream -> deque of waiting job indices
-        busy = np.zeros(self.max_streams, bool)
-        ready: deque = deque()            # streams free with a job waiting
-        act_job = np.empty(0, np.int64)
-        act_stream = np.empty(0, np.uint32)
-        act_done = np.empty(0, np.int64)
-        act_buf = np.empty(0, np.uint64)
-        n_waiting = 0
+        S = self.max_streams
+        # per stream (indexed by stream id), bits counted from the chain's start
+        done = np.zeros(S, np.int64)      # produced
+        end = np.zeros(S, np.int64)       # admitted (end of the last request in the chain)
+        cur_end = np.zeros(S, np.int64)   # end of the first unfinished request
+        cur_start = np.zeros(S, np.int64)
+        cur_buf = np.zeros(S, np.uint64)  # its output buffer (keep_outputs)
+        chains: dict = {}                 # stream -> deque of [job, start, end, buf]
+        waiting: deque = deque()          # arrived, not yet admitted (keep_outputs budget)
         inflight: deque = deque()
         used = 0
         served = 0
+        busy_ms = 0.0                     # device time spent in steps
         t0 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         t0.record(self.stream)
         t_start = time.perf_counter()
         nxt = 0
-
-        busy_ms = 0.0                     # device time spent in steps
 
         def retire(block: bool):
             nonlocal used, busy_ms
@@ -165,79 +168,71 @@ class Server:
                 retire(block=True)
             used += nb
 
-        while nxt < n or n_waiting or act_job.size or inflight:
+        def admit(j) -> bool:
+            """Append job j to its stream's chain; False if the budget blocks it."""
+            nonlocal used
+            r = requests[j]
+            sid = r.stream_id
+            ident = self.identity.get(sid)
+            if ident is not None and ident != (r.key, r.iv, r.iv_len):
+                rejected[j] = True                 # key/IV differ from the resident stream's
+                return True
+            nb = int(bits[j]) // 8
+            if self.keep_outputs and used > 0 and used + nb > self.budget:
+                return False                       # wait for buffers to be released
+            if ident is None:
+                self.identity[sid] = (r.key, r.iv, r.iv_len)
+                new_js.append(j)
+            if bits[j] == 0:
+                finish[j] = 1e3 * (time.perf_counter() - t_start)
+                return True
+            buf = 0
+            if self.keep_outputs:
+                t = torch.empty(nb, dtype=torch.uint8, device=self.stream.device)
+                self.outputs[j] = t
+                buf = t.data_ptr()
+                used += nb
+            q = chains.setdefault(sid, deque())
+            a, b = int(end[sid]), int(end[sid] + bits[j])
+            if not q:                              # the stream was idle
+                cur_start[sid], cur_end[sid], cur_buf[sid] = a, b, buf
+            q.append([j, a, b, buf])
+            end[sid] = b
+            return True
+
+        while nxt < n or waiting or inflight or (end > done).any():
             now = time.perf_counter() - t_start
             while nxt < n and (not realtime or arrival[nxt] <= now):
-                sid = requests[nxt].stream_id
                 release[nxt] = 1e3 * now
-                q = queues.setdefault(sid, deque())
-                if not q and not busy[sid]:
-                    ready.append(sid)
-                q.append(nxt)
-                n_waiting += 1
+                waiting.append(nxt)
                 nxt += 1
             retire(block=len(inflight) >= self.max_inflight)
-            # admission: the first waiting job of every free stream
-            new_js, adm, adm_buf = [], [], []
-            while ready:
-                sid = ready.popleft()
-                q = queues[sid]
-                while q:
-                    j = q[0]
-                    r = requests[j]
-                    ident = self.identity.get(sid)
-                    if ident is not None and ident != (r.key, r.iv, r.iv_len):
-                        q.popleft()
-                        n_waiting -= 1
-                        rejected[j] = True         # key/IV differ from the resident stream's
-                        continue
-                    nb = int(bits[j]) // 8
-                    if self.keep_outputs and used > 0 and used + nb > self.budget:
-                        break                      # wait for buffers to be released
-                    q.popleft()
-                    n_waiting -= 1
-                    if ident is None:
-                        self.identity[sid] = (r.key, r.iv, r.iv_len)
-                        new_js.append(j)
-                    if bits[j] == 0:
-                        finish[j] = 1e3 * (time.perf_counter() - t_start)
-                        continue
-                    buf = 0
-                    if self.keep_outputs:
-                        t = torch.empty(nb, dtype=torch.uint8, device=self.stream.device)
-                        self.outputs[j] = t
-                        buf = t.data_ptr()
-                        used += nb
-                    busy[sid] = True
-                    adm.append(j)
-                    adm_buf.append(buf)
-                    break
-                if q and not busy[sid]:
-                    ready.appendleft(sid)          # blocked by the budget
-                    break
+            new_js = []
+            while waiting and admit(waiting[0]):
+                waiting.popleft()
             if new_js:
                 self._init_streams(requests, new_js)
-            if adm:
-                act_job = np.concatenate((act_job, np.array(adm, np.int64)))
-                act_stream = np.concatenate((act_stream, np.array(
-                    [requests[j].stream_id for j in adm], np.uint32)))
-                act_done = np.concatenate((act_done, np.zeros(len(adm), np.int64)))
-                act_buf = np.concatenate((act_buf, np.array(adm_buf, np.uint64)))
-            if act_job.size:
-                ev0, ev, arena, b = self._issue(act_stream, act_done, bits[act_job], act_buf,
-                                                reserve)
-                served += b
-                done = act_done == bits[act_job]
-                fin = act_job[done]
+            act = np.flatnonzero(end > done).astype(np.uint32)
+            if act.size:
+                lim = cur_end if self.keep_outputs else end
+                rem = lim[act] - done[act]
+                ptr = cur_buf[act] + ((done[act] - cur_start[act]) // 8).astype(np.uint64)
+                ev0, ev, arena, order, k_lane = self._issue(act, rem, ptr, reserve)
+                served += int(k_lane.sum())
+                lanes = act[order]
+                done[lanes] += k_lane
+                fin = []
+                for sid in lanes[done[lanes] >= cur_end[lanes]]:
+                    q = chains[int(sid)]
+                    while q and q[0][2] <= done[sid]:
+                        fin.append(q.popleft()[0])
+                    if q:
+                        cur_start[sid], cur_end[sid], cur_buf[sid] = q[0][1], q[0][2], q[0][3]
+                    else:                          # chain empty: restart its counts
+                        done[sid] = end[sid] = cur_end[sid] = cur_start[sid] = 0
+                fin = np.array(fin, np.int64)
                 inflight.append((ev0, ev, fin, int(bits[fin].sum()) // 8 if arena is None
                                  else arena.numel()))
-                for sid in act_stream[done]:
-                    busy[sid] = False
-                    if queues[int(sid)]:
-                        ready.append(int(sid))
-                keep = ~done
-                act_job, act_done, act_buf = act_job[keep], act_done[keep], act_buf[keep]
-                act_stream = act_stream[keep]
                 del arena          # the caching allocator reuses it after the step
             elif inflight:
                 retire(block=True)
