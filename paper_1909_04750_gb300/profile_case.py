@@ -13,6 +13,12 @@ come first).
 ``split``: a batch of n streams of ``n_bits`` each whose groups all take the
 one-warp-per-group path (split threshold 1 clock), run ``--reps`` times.
 
+``batched``: the 100,000-stream ragged batch (seed 3), autotuned (cached),
+replayed ``--reps`` times.
+
+``lfsr``: Fibonacci LFSRs of degree 64 (x^64 + x^4 + x^3 + x + 1), n
+instances x ``n_bits``, ``--reps`` times.
+
 ``crc8``: CRC-8 (0x1D, preset and final XOR 0xFF) of n messages of
 ``n_bits / 8`` bytes each (random, device-resident), ``--reps`` times.
 
@@ -36,10 +42,33 @@ def main():
     p.add_argument("--n-bits", type=int, default=2048)
     p.add_argument("--layout", default="bytes")
     p.add_argument("--reps", type=int, default=2)
-    p.add_argument("--case", choices=("plain", "split", "serve", "crc8"), default="plain")
+    p.add_argument("--case", choices=("plain", "split", "serve", "crc8", "batched", "lfsr"),
+                   default="plain")
     p.add_argument("--autotune", action="store_true")
     a = p.parse_args()
     build()
+    if a.case == "batched":
+        from .batch import Batch, tune
+        s = workloads.batched()
+        k, v = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
+        b = Batch(s.n_bits, s.iv_lens)
+        out = torch.empty(b.output_bytes, dtype=torch.uint8, device="cuda")
+        print("config:", tune(b, k, v, out))
+        for _ in range(a.reps):
+            b.run(k, v, out)
+        b.sync()
+        print("ok", vars(a))
+        return
+    if a.case == "lfsr":
+        from .lfsr import lfsr_generate
+        g = torch.Generator(device="cuda").manual_seed(5)
+        seeds = torch.randint(1, 1 << 62, (a.n,), dtype=torch.int64, device="cuda", generator=g)
+        out = torch.empty((a.n_bits, (a.n + 31) // 32), dtype=torch.int32, device="cuda")
+        for _ in range(a.reps):
+            lfsr_generate(seeds, 64, 0b11011, a.n_bits, out=out)
+        torch.cuda.synchronize()
+        print("ok", vars(a))
+        return
     if a.case == "crc8":
         from .lfsr import crc8
         g = torch.Generator(device="cuda").manual_seed(5)
