@@ -76,8 +76,9 @@ class Server:
                                                    ivs.ctypes.data, lens.ctypes.data, len(js)))
 
     def _plan(self, rem):
-        """Groups of the sorted active requests: (order, group of each
-        served lane, bits per group, split-group count)."""
+        """Plan a step over the active streams with `rem` bits left each:
+        (order of the served streams, longest first; bits per 32-lane group;
+        number of split groups, which lead the order)."""
         order = np.argsort(-rem, kind="stable")
         n = order.size
         ns = min((int(np.count_nonzero(rem >= self.split_min_bits)) + 31) // 32,
