@@ -197,6 +197,11 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # one rank compiles (if anything is stale) while the others wait, so no
+    # two processes write the same build directory
+    if rank == 0:
+        build()
+    shard.barrier()
     build()
     n, n_bits = args.n, args.n_bits
     # weak scaling: rank r runs its own 2^20 instances (draws offset by rank)
