@@ -108,7 +108,7 @@ def test_batched_workload_full_size_sampled():
     order = np.argsort(-s.n_bits.astype(np.int64), kind="stable")
     rng = np.random.default_rng(3)
     pick = sorted(set(order[:8].tolist()) | set(order[-8:].tolist()) |
-                  set(rng.integers(0, s.n, 120).tolist()))
+                  set(rng.integers(0, s.n, 4096).tolist()))
     _check(b, out, s, idx=pick)
     # every IV length bucket is represented
     assert set(s.iv_lens[pick]) == {0, 16, 32, 48, 64, 80}

@@ -230,7 +230,7 @@ def test_plain_scale_full_size_sampled():
     st.reset(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
     bs = st.generate(n_bits, "bitsliced")
     st.sync()
-    rows = _sample_rows(s.n, 1024, 11)
+    rows = _sample_rows(s.n, 4096, 11)
     sub = s.subset(rows)
     ref = _ref(sub, n_bits)
     got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
@@ -262,7 +262,7 @@ def test_fused_full_size_sampled():
     # property on every output word: f == (u >> 8) * 2^-24, exactly
     chk = (u.view(torch.int32) >> 8) & 0xFFFFFF
     assert bool(torch.equal(chk.to(torch.float32) * (2.0 ** -24), f))
-    rows = _sample_rows(s.n, 1024, 13)
+    rows = _sample_rows(s.n, 4096, 13)
     ref = oracle.to_u32(_ref(s.subset(rows), n_bits), n_bits)
     got = u[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.uint32)
     assert _first_diff(got, ref) is None
