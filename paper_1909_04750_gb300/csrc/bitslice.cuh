@@ -132,10 +132,11 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
 // (see the keystream kernels).
 template <int J>
 __device__ __forceinline__ void swap_bits(uint32_t &lo, uint32_t &hi) {
+  // two independent bit-selects, (x & ~m) | (y & m) = truth table 0xD8
   constexpr uint32_t m = J == 4 ? 0x0F0F0F0Fu : J == 2 ? 0x33333333u : 0x55555555u;
-  const uint32_t t = (lo ^ (hi >> J)) & m;
-  lo ^= t;
-  hi ^= t << J;
+  const uint32_t x = lo, y = hi;
+  lo = lop3<0xD8>(x, y >> J, m);
+  hi = lop3<0xD8>(y, x << J, m << J);
 }
 // Block swap of size 16: lo keeps its high half and takes hi's high half;
 // hi keeps its low half and takes lo's low half.
