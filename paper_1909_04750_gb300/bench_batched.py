@@ -68,6 +68,9 @@ def main():
                    help="plain-workload throughput for the work bound (measured if absent)")
     p.add_argument("--steady", type=int, default=0, help="batches for the steady-state rate")
     p.add_argument("--pipeline", type=int, default=4, help="handles (CUDA streams) in flight")
+    p.add_argument("--steady-split", type=int, default=0,
+                   help="split threshold for the steady-state run as max_clocks / this "
+                        "(0: the tuned one)")
     a = p.parse_args()
     build()
     s = workloads.batched(a.n)
@@ -104,7 +107,11 @@ def main():
     if a.plain_gbit_s:
         line["work_bound_ms"] = bits / (a.plain_gbit_s * 1e9) * 1e3
     if a.steady:
-        line["steady"] = steady_state(b, s, keys, ivs, tuned, a.steady, a.pipeline)
+        cfg = dict(tuned)
+        if a.steady_split:
+            cfg["split_clocks"] = b.max_clocks // a.steady_split
+        line["steady"] = steady_state(b, s, keys, ivs, cfg, a.steady, a.pipeline)
+        line["steady"]["split_clocks"] = cfg["split_clocks"]
     print(json.dumps(line), flush=True)
     b.free()
 
