@@ -28,7 +28,7 @@
  *             (80), then 100 mixing clocks with input 0;
  *   keystream z = r0 ^ s0 taken before each non-mixing, zero-input clock.
  *
- * Readings where the paper is silent (all are stated again in the design doc):
+ * Readings where the paper is silent:
  *   - key bit k_i / IV bit iv_i is bit (7 - i%8) of byte i/8 (MSB first);
  *   - keystream bit z_t is written MSB-first: bit (7 - t%8) of byte t/8;
  *   - IV length is any integer 0..80 bits; the key is exactly 80 bits.
