@@ -312,7 +312,7 @@ int copy_inputs(mickey_batch *b, const void *keys, const void *ivs, int mem) {
       mem == MICKEY_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (cudaMemcpyAsync(b->d_in, keys, 10 * b->n, kind, b->stream) != cudaSuccess ||
       cudaMemcpyAsync(b->d_in + 10 * b->n, ivs, 10 * b->n, kind, b->stream) != cudaSuccess)
-    return MICKEY_E_CUDA;
+    return set_error(MICKEY_E_CUDA, "key/IV upload");
   return MICKEY_OK;
 }
 
@@ -408,14 +408,14 @@ MICKEY_API size_t mickey_batch_output_bytes(const mickey_batch *b) {
 }
 
 MICKEY_API int mickey_batch_offsets(const mickey_batch *b, uint64_t *offsets) {
-  if (!b || !offsets) return MICKEY_E_ARG;
+  if (!b || !offsets) return set_error(MICKEY_E_ARG, "NULL argument");
   std::memcpy(offsets, b->offsets.data(), b->n * 8);
   return MICKEY_OK;
 }
 
 MICKEY_API int mickey_batch_clocks(const mickey_batch *b, uint64_t *max_clocks,
                                    uint64_t *total_clocks) {
-  if (!b) return MICKEY_E_ARG;
+  if (!b) return set_error(MICKEY_E_ARG, "NULL handle");
   if (max_clocks) *max_clocks = b->max_clocks;
   if (total_clocks) *total_clocks = b->total_clocks;
   return MICKEY_OK;
@@ -423,22 +423,24 @@ MICKEY_API int mickey_batch_clocks(const mickey_batch *b, uint64_t *max_clocks,
 
 MICKEY_API int mickey_batch_run(mickey_batch *b, const void *keys, const void *ivs, void *out,
                                 int mem) {
-  if (!b || !keys || !ivs || !out) return MICKEY_E_ARG;
-  if (mem != MICKEY_MEM_HOST && mem != MICKEY_MEM_DEVICE) return MICKEY_E_ARG;
+  if (!b || !keys || !ivs || !out) return set_error(MICKEY_E_ARG, "NULL argument");
+  if (mem != MICKEY_MEM_HOST && mem != MICKEY_MEM_DEVICE)
+    return set_error(MICKEY_E_ARG, "mem must be MICKEY_MEM_HOST or MICKEY_MEM_DEVICE");
   int rc = copy_inputs(b, keys, ivs, mem);
   if (rc) return rc;
   BatchParams p{static_cast<uint8_t *>(out)};
   if (cudaMemcpyAsync(b->d_params, &p, sizeof p, cudaMemcpyHostToDevice, b->stream) !=
           cudaSuccess ||
       cudaGraphLaunch(b->exec, b->stream) != cudaSuccess)
-    return MICKEY_E_CUDA;
-  return MICKEY_OK;
+    return set_error(MICKEY_E_CUDA, "graph launch");
+  return set_error(MICKEY_OK, "");
 }
 
 MICKEY_API int mickey_batch_set_config(mickey_batch *b, int unroll, int blocks_per_sm,
                                        uint64_t split_clocks) {
-  if (!b || !valid_unroll(unroll) || blocks_per_sm < 1 || blocks_per_sm > 2) return MICKEY_E_ARG;
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MICKEY_E_CUDA;
+  if (!b || !valid_unroll(unroll) || blocks_per_sm < 1 || blocks_per_sm > 2)
+    return set_error(MICKEY_E_ARG, "unroll must be 2 or 4, blocks_per_sm 1 or 2");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(MICKEY_E_CUDA, "sync");
   b->unroll = unroll;
   b->blocks_per_sm = blocks_per_sm;
   b->split_clocks = split_clocks;
@@ -451,7 +453,7 @@ MICKEY_API int mickey_batch_set_config(mickey_batch *b, int unroll, int blocks_p
 
 MICKEY_API int mickey_batch_get_config(const mickey_batch *b, int *unroll, int *blocks_per_sm,
                                        uint64_t *split_clocks, uint32_t *split_groups) {
-  if (!b || !unroll || !blocks_per_sm) return MICKEY_E_ARG;
+  if (!b || !unroll || !blocks_per_sm) return set_error(MICKEY_E_ARG, "NULL argument");
   *unroll = b->unroll;
   *blocks_per_sm = b->blocks_per_sm;
   if (split_clocks) *split_clocks = b->split_clocks;
@@ -460,15 +462,17 @@ MICKEY_API int mickey_batch_get_config(const mickey_batch *b, int *unroll, int *
 }
 
 MICKEY_API int mickey_batch_sync(mickey_batch *b) {
-  if (!b) return MICKEY_E_ARG;
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MICKEY_E_CUDA;
+  if (!b) return set_error(MICKEY_E_ARG, "NULL handle");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(MICKEY_E_CUDA, "sync");
   int flag = 0;
-  if (cudaMemcpy(&flag, b->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return MICKEY_E_CUDA;
+  if (cudaMemcpy(&flag, b->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_error(MICKEY_E_CUDA, "D2H err");
   if (flag) {
     cudaMemset(b->d_err, 0, 4);
-    return (flag & kErrIvLen) ? MICKEY_E_IVLEN : MICKEY_E_TIMEOUT;
+    return (flag & kErrIvLen) ? set_error(MICKEY_E_IVLEN, "an IV length above 80 bits was given")
+                              : set_error(MICKEY_E_TIMEOUT, "a device-side wait timed out");
   }
-  return MICKEY_OK;
+  return set_error(MICKEY_OK, "");
 }
 
 MICKEY_API void mickey_batch_free(mickey_batch *b) { batch_release(b); }
