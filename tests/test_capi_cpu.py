@@ -161,3 +161,15 @@ def test_lfsr_and_crc_reject_bad_arguments_on_the_host(L):
     assert L.mickey_crc8(p, 4, 4, 7, 0, 0, None, N.MEM_HOST, None) == N.E_ARG   # crc
     assert L.mickey_crc8(p, 4, 4, 7, 0, 0, o, 5, None) == N.E_ARG                     # mem kind
     assert L.mickey_crc8(p, 0, 4, 7, 0, 0, o, N.MEM_HOST, None) == N.OK               # nothing to do
+
+
+def test_plain_c_program_compiles_and_links(L, tmp_path):
+    # include/mickey.h is valid C11 and the library resolves every symbol a C
+    # user needs (the program runs in the GPU tests)
+    import subprocess
+    exe = str(tmp_path / "generate_c")
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi", "generate_c.c"), "-o", exe,
+                    "-L", os.path.dirname(B.LIB), "-lmickey",
+                    "-Wl,-rpath," + os.path.dirname(B.LIB)], check=True)
+    assert os.path.exists(exe)

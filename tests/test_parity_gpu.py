@@ -350,3 +350,23 @@ def test_persistent_wait_runs_out_without_a_fault(monkeypatch):
     ok.sync()
     rows = _sample_rows(s.n, 48, 6)
     assert np.array_equal(got[rows], _ref(s.subset(rows), 1000)[:, :125])
+
+
+def test_plain_c_program_through_the_abi(tmp_path):
+    # a C user of include/mickey.h, built with gcc against the in-tree
+    # library, generates the 32-instance workload into host memory
+    import subprocess
+    from paper_1909_04750_gb300 import build as B
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = str(tmp_path / "generate_c")
+    subprocess.run(["gcc", "-std=c11", "-O1", "-I", os.path.join(root, "include"),
+                    os.path.join(root, "tests", "c_abi", "generate_c.c"), "-o", exe,
+                    "-L", os.path.dirname(B.LIB), "-lmickey",
+                    "-Wl,-rpath," + os.path.dirname(B.LIB)], check=True)
+    s = workloads.plain_small()
+    (tmp_path / "in.bin").write_bytes(s.keys.tobytes() + s.ivs.tobytes())
+    n_bits = 4096 + 13                                   # ragged last byte
+    subprocess.run([exe, str(tmp_path / "in.bin"), str(s.n), str(n_bits),
+                    str(tmp_path / "out.bin")], check=True)
+    got = np.frombuffer((tmp_path / "out.bin").read_bytes(), np.uint8).reshape(s.n, -1)
+    assert np.array_equal(got, _ref(s, n_bits))
