@@ -165,13 +165,16 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
 /* --------------------------------------------------------------------------
  * Launch configuration and autotuning of the keystream kernel (per layout).
  *   mode    MICKEY_MODE_GRID: one thread per 32-lane group, 4 warps per block;
- *           MICKEY_MODE_PERSISTENT: one warp per SM sub-partition, the
- *           groups x tiles work line cut into equal segments (used only when
- *           there are at least as many 1024-instance warp-groups as warps);
- *           MICKEY_MODE_PERSISTENT2: the same with two warps per SM
- *           sub-partition (two blocks per SM, rows staged four tiles deep);
- *           MICKEY_MODE_AUTO: persistent when the grid launch would leave
- *           much of its last wave empty.
+ *           MICKEY_MODE_PERSISTENT: one clock warp per SM sub-partition,
+ *           paired with an emission warp that transposes and stores its
+ *           tiles, the groups x tiles work line cut into equal segments
+ *           (used only when there are at least as many 1024-instance
+ *           warp-groups as clock warps);
+ *           MICKEY_MODE_PERSISTENT2: two warps per SM sub-partition, each
+ *           clocking and emitting (two blocks per SM, rows staged four
+ *           tiles deep);
+ *           MICKEY_MODE_AUTO: persistent whenever there are at least as
+ *           many warp-groups as clock warps, else grid.
  *   unroll  clocks per inner step, 2 or 4.
  *   stage   row layouts: stage four 32-bit words per row in shared memory
  *           and write 16-byte chunks (needs n_bits % 128 == 0).
@@ -179,8 +182,8 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
  * persistent, persistent2), MICKEY_UNROLL (2, 4), MICKEY_STAGE (0, 1) and
  * MICKEY_PERSIST_BLOCKS (fewer persistent blocks than SMs) set the defaults;
  * MICKEY_SPIN_LIMIT bounds a persistent tail piece's wait for its head
- * (polls of about 256 ns, default 2^24), after which the piece is skipped and
- * mickey_sync reports MICKEY_E_TIMEOUT; MICKEY_TEST_UNPUBLISHED=1 is a test
+ * (polls of about 256 ns, default 2^24), after which mickey_sync reports
+ * MICKEY_E_TIMEOUT and that call's output and state are undefined; MICKEY_TEST_UNPUBLISHED=1 is a test
  * hook that makes every such wait run out (tails wait for a value no head
  * writes), to exercise that path without a fault.
  * ------------------------------------------------------------------------ */
@@ -356,6 +359,17 @@ MICKEY_API int mickey_ops_per_clock(int mixing);
  * (MHz), and the whole-GPU rate in 10^12 ops/s. */
 MICKEY_API int mickey_probe_lop3(int blocks_per_sm, int threads, int iters,
                                  double *ops_per_sm_clk, double *sm_mhz, double *tops);
+
+/* Measurement helper: the bare bitsliced keystream clock (z = r0 ^ s0 and
+ * one CLOCK_KG, no output) of blocks_per_sm (1 or 2) * SM-count blocks of
+ * 128 threads, one 32-lane group per thread, on a state of arbitrary words,
+ * `clocks` clocks per group (a multiple of 4, >= 4), synchronously on the
+ * current device.  Outputs (each may be NULL): algorithmic logic ops
+ * (mickey_ops_per_clock(0) per group-clock) per SM per SM-cycle, and the
+ * SM clock seen (MHz).  The ceiling the keystream kernel's clock can reach
+ * with one (or two) warps per SM sub-partition. */
+MICKEY_API int mickey_probe_clock(int blocks_per_sm, int clocks, double *ops_per_sm_clk,
+                                  double *sm_mhz);
 
 /* Library version string. */
 MICKEY_API const char *mickey_version(void);

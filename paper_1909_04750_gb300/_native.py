@@ -60,6 +60,7 @@ SIGNATURES = {
     "mickey_ops_per_clock": (c_int, [c_int]),
     "mickey_version": (c_char_p, []),
     "mickey_probe_lop3": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "mickey_probe_clock": (c_int, [c_int, c_int, c_void_p, c_void_p]),
     "mickey_set_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "mickey_get_config": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "mickey_tune": (c_int, [c_void_p, c_uint64, c_int, c_void_p, c_int, c_void_p]),

@@ -4,7 +4,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -228,11 +227,6 @@ int check_generate(const mickey_streams *s, uint64_t n_bits, const void *out, in
   return check_limit(s, n_bits);
 }
 
-// Whether a launch of `bits` clocks should use the persistent kernel: only
-// when there are at least as many warp-groups as warps (one per SM
-// sub-partition) and the grid launch would leave a large part of its last
-// wave empty (a lone warp per sub-partition runs at ~95 % of the rate of
-// two, so below that the grid launch wins).
 bool is_persistent(int mode) {
   return mode == MICKEY_MODE_PERSISTENT || mode == MICKEY_MODE_PERSISTENT2;
 }
@@ -240,14 +234,15 @@ bool is_persistent(int mode) {
 // Blocks per SM of a persistent launch in `mode`.
 uint32_t persist_per_sm(int mode) { return mode == MICKEY_MODE_PERSISTENT2 ? 2u : 1u; }
 
+// Whether a launch should use a persistent kernel: whenever there are at
+// least as many warp-groups as clock warps.  With its clock warps relieved
+// of the emission, the one-block-per-SM persistent launch outruns the grid
+// launch at every size measured (2^20 to 2^24 instances), so AUTO takes it.
 bool use_persistent(const mickey_streams *s, int mode) {
   const uint64_t W = (s->G + 31) / 32;
   const uint64_t slots = uint64_t(s->persist_blocks) * persist_per_sm(mode) * 4;
   if (mode == MICKEY_MODE_GRID || W < slots) return false;
-  if (is_persistent(mode)) return true;
-  const double waves = double((s->G + kKsThreads - 1) / kKsThreads) / (2.0 * s->sm_count);
-  const double eff = waves / std::ceil(waves);
-  return eff < 0.93;
+  return true;
 }
 
 // One keystream launch of `bits` clocks into a device buffer.

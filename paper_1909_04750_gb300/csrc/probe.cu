@@ -3,11 +3,15 @@
 // (inline PTX so that nothing folds); each block measures its own SM-cycle
 // count with clock64.  ops per SM per cycle = ops of the resident blocks on
 // one SM / cycles, independent of the clock the GPU ran at.
+//
+// Bare-clock probe: the keystream kernel's clock loop without any output,
+// the ceiling its clock warps can reach.
 #include <cuda_runtime.h>
 
 #include <vector>
 
 #include "../../include/mickey.h"
+#include "bitslice.cuh"
 
 namespace {
 
@@ -39,7 +43,88 @@ __global__ void lop3_probe_kernel(uint32_t seed, int iters, uint32_t *sink,
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// One group per thread: load 200 words (word-major, G words apart), run
+// `clocks` keystream clocks folding every z word into an accumulator, write
+// the state and the accumulator back (so nothing is dead code).
+__global__ void __launch_bounds__(128, 1)
+    clock_probe_kernel(uint32_t *state, uint32_t *acc_out, int clocks, long long *cycles) {
+  const uint32_t G = gridDim.x * blockDim.x;
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t r[mickey::kReg], s[mickey::kReg];
+#pragma unroll
+  for (int i = 0; i < mickey::kReg; ++i) {
+    r[i] = state[size_t(i) * G + g];
+    s[i] = state[size_t(mickey::kReg + i) * G + g];
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  uint32_t acc = 0;
+#pragma unroll 1
+  for (int c = 0; c < clocks; c += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc = mickey::lop3<0x96>(acc, r[0], s[0]);
+      mickey::clock_kg<false, false>(r, s, 0u, 0u);
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+#pragma unroll
+  for (int i = 0; i < mickey::kReg; ++i) {
+    state[size_t(i) * G + g] = r[i];
+    state[size_t(mickey::kReg + i) * G + g] = s[i];
+  }
+  acc_out[g] = acc;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace
+
+extern "C" MICKEY_API int mickey_probe_clock(int blocks_per_sm, int clocks, double *ops_per_sm_clk,
+                                             double *sm_mhz) {
+  if (blocks_per_sm < 1 || blocks_per_sm > 2 || clocks < 4 || clocks % 4) return MICKEY_E_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MICKEY_E_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MICKEY_E_CUDA;
+  const int blocks = sms * blocks_per_sm;
+  const size_t G = size_t(blocks) * 128;
+  uint32_t *state = nullptr, *acc = nullptr;
+  long long *cyc = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = MICKEY_OK;
+  if (cudaMalloc(&state, G * 200 * 4) != cudaSuccess || cudaMalloc(&acc, G * 4) != cudaSuccess ||
+      cudaMalloc(&cyc, blocks * sizeof(long long)) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = MICKEY_E_CUDA;
+  } else {
+    // any state will do: a byte pattern that is neither all zeros nor all ones
+    cudaMemset(state, 0x5a, G * 200 * 4);
+    clock_probe_kernel<<<blocks, 128>>>(state, acc, 64, cyc);  // warm-up
+    cudaEventRecord(e0);
+    clock_probe_kernel<<<blocks, 128>>>(state, acc, clocks, cyc);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = MICKEY_E_CUDA;
+    } else {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      std::vector<long long> h(blocks);
+      cudaMemcpy(h.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+      long long mx = 0;
+      for (long long c : h) mx = c > mx ? c : mx;
+      const double ops_sm = 128.0 * blocks_per_sm * double(clocks) * mickey::ops_per_clock(false);
+      if (ops_per_sm_clk) *ops_per_sm_clk = ops_sm / double(mx);
+      if (sm_mhz) *sm_mhz = double(mx) / (ms * 1e3);
+    }
+  }
+  cudaFree(state);
+  cudaFree(acc);
+  cudaFree(cyc);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}
 
 extern "C" MICKEY_API int mickey_probe_lop3(int blocks_per_sm, int threads, int iters,
                                             double *ops_per_sm_clk, double *sm_mhz,

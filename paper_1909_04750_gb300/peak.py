@@ -1,4 +1,5 @@
-"""Measure the GPU's 3-input LOP3 rate (the keystream roofline's peak).
+"""Measure the GPU's 3-input LOP3 rate (the keystream roofline's peak) and
+the rate of the bare bitsliced clock (the ceiling of the keystream kernel).
 
     python -m paper_1909_04750_gb300.peak
 """
@@ -31,6 +32,13 @@ def main():
                                     ctypes.byref(c)))
         print("blocks/SM=%d threads=%d: %.1f LOP3/SM/clk at %.0f MHz, %.2f T ops/s"
               % (bps, thr, a.value, b.value, c.value), flush=True)
+    # the bare keystream clock: the ceiling of the kernel's clock warps
+    for bps in (1, 2):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        N.check(L.mickey_probe_clock(bps, 8192, ctypes.byref(a), ctypes.byref(b)))
+        print("bare clock, %d warp(s) per SM sub-partition: %.1f algorithmic ops/SM/clk "
+              "= %.3f of %.0f, at %.0f MHz" % (bps, a.value, a.value / LOP3_PER_SM_CLK,
+                                               LOP3_PER_SM_CLK, b.value), flush=True)
 
 
 if __name__ == "__main__":

@@ -90,6 +90,9 @@ def test_invalid_arguments_rejected_on_host(L):
     L.mickey_free(None)
     assert L.mickey_error_string(N.E_LIMIT) == b"more than 2^40 keystream bits for one key/IV"
     assert L.mickey_version().startswith(b"mickey-gb300")
+    # the bare-clock probe checks its arguments before touching a device
+    for bps, clocks in ((0, 64), (3, 64), (1, 0), (1, 6)):
+        assert L.mickey_probe_clock(bps, clocks, None, None) == N.E_ARG
 
 
 def _plan_only(**kw):

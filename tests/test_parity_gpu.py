@@ -370,3 +370,21 @@ def test_plain_c_program_through_the_abi(tmp_path):
                     str(tmp_path / "out.bin")], check=True)
     got = np.frombuffer((tmp_path / "out.bin").read_bytes(), np.uint8).reshape(s.n, -1)
     assert np.array_equal(got, _ref(s, n_bits))
+
+
+# -------------------------------------------------------------- roofline probes
+
+def test_roofline_probes_stay_below_the_lop3_rate():
+    # the LOP3 probe measures the denominator (64 per SM per clock); the bare
+    # keystream clock (327 algorithmic ops per group-clock) can come close to
+    # it but not above, else the op count or the probe would be wrong
+    import ctypes
+    L = N.lib()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    N.check(L.mickey_probe_lop3(1, 128, 2000, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    assert 56.0 < a.value <= 64.5, a.value
+    for bps in (1, 2):
+        x, mhz = ctypes.c_double(), ctypes.c_double()
+        N.check(L.mickey_probe_clock(bps, 1024, ctypes.byref(x), ctypes.byref(mhz)))
+        assert 40.0 < x.value <= 64.5, (bps, x.value)
+        assert 500.0 < mhz.value < 2200.0, mhz.value
