@@ -34,7 +34,12 @@ extern "C" {
  *           instance 32g + l (lanes past n_inst are 0); n_bits * G u32 words.
  *   stream  cudaStream_t (NULL: the default stream); asynchronous.
  * Returns 0, MICKEY_E_ARG (NULL pointer, n_inst or n_bits 0, degree outside
- * 2..64, taps outside the degree or a_0 = 0) or MICKEY_E_CUDA. */
+ * 2..64, taps outside the degree or a_0 = 0) or MICKEY_E_CUDA.
+ * Up to 16 taps run in a kernel that reads only the taps' words (k - 1
+ * XORs per clock), more in one that XORs all `degree` words under masks;
+ * both give the same words.  Test hooks read at each call:
+ * MICKEY_LFSR_DENSE=1 forces the mask kernel, MICKEY_LFSR_NOBATCH=1 makes
+ * the few-tap kernel clock one step at a time. */
 MICKEY_API int mickey_lfsr_generate(const uint64_t *seeds, size_t n_inst, int degree,
                                     uint64_t taps, uint64_t n_bits, uint32_t *out, int mem,
                                     void *stream);

@@ -5,9 +5,12 @@
 CRC-8 (polynomial 0x1D, preset and final XOR 0xFF) of 2^20 messages of
 1 KiB each (1 GiB, device-resident, far larger than L2): GB/s of message
 bytes and the fraction of the measured HBM copy rate (the kernel reads each
-byte once).  Fibonacci LFSRs of degree 64 (x^64 + x^4 + x^3 + x + 1), 2^20
-instances x 4096 bits: Gbit/s and the fraction of the LOP3 roofline (64
-logic ops per clock per 32 instances at degree 64).  CUDA events; best of K.
+byte once).  Fibonacci LFSRs of degree 64, 2^20 instances x 4096 bits:
+with the four taps of x^64 + x^4 + x^3 + x + 1 (the sparse-tap kernel:
+Gbit/s and the fraction of the measured HBM copy rate, the output words
+being the only traffic that grows with the run), and the same LFSRs run
+through the mask kernel (Gbit/s and the fraction of the LOP3 roofline: 64
+logic ops per clock per 32 instances).  CUDA events; best of K.
 """
 import argparse
 import json
@@ -60,17 +63,31 @@ def main():
     ni, nb, d = 1 << 20, 4096, 64
     seeds = torch.randint(1, 1 << 62, (ni,), dtype=torch.int64, device="cuda", generator=g)
     out = torch.empty((nb, (ni + 31) // 32), dtype=torch.int32, device="cuda")
-    ms2 = _best_ms(lambda: lfsr.lfsr_generate(seeds, d, 0b11011, nb, out=out), a.reps)
+    taps = 0b11011                                  # a_0, a_1, a_3, a_4
+    ms2 = _best_ms(lambda: lfsr.lfsr_generate(seeds, d, taps, nb, out=out), a.reps)
+    out_bytes = out.numel() * 4 + ni * 8              # output words + seeds read
+    os.environ["MICKEY_LFSR_DENSE"] = "1"              # the same LFSRs, mask kernel
+    try:
+        ms3 = _best_ms(lambda: lfsr.lfsr_generate(seeds, d, taps, nb, out=out), a.reps)
+    finally:
+        del os.environ["MICKEY_LFSR_DENSE"]
     ops = (ni // 32) * (nb - d) * 64
+    lfsr_gbs = out_bytes / (ms2 * 1e-3) / 1e9
     print(json.dumps({
         "crc8": {"messages": n, "bytes_each": ln, "ms": ms, "gb_s": gbs,
                  "hbm_frac": gbs / hbm if hbm else None,
                  "hbm_peak_gb_s": hbm, "peak_basis": "MEASURED_PEAKS.json hbm_gbs, of measured"},
-        "lfsr": {"instances": ni, "degree": d, "bits_each": nb, "ms": ms2,
-                 "gbit_s": ni * nb / (ms2 * 1e-3) / 1e9,
-                 "roofline": {"bound": "alu", "achieved_tops": ops / (ms2 * 1e-3) / 1e12,
-                              "peak_tops": lop3_peak_tops(),
-                              "frac": ops / (ms2 * 1e-3) / 1e12 / lop3_peak_tops()}},
+        "lfsr": {"instances": ni, "degree": d, "taps": 4, "bits_each": nb, "ms": ms2,
+                 "kernel": "lfsr_sparse_kernel", "gbit_s": ni * nb / (ms2 * 1e-3) / 1e9,
+                 "roofline": {"bound": "hbm", "achieved_gb_s": lfsr_gbs, "peak_gb_s": hbm,
+                              "frac": lfsr_gbs / hbm if hbm else None,
+                              "bytes": out_bytes}},
+        "lfsr_mask_kernel": {"instances": ni, "degree": d, "bits_each": nb, "ms": ms3,
+                             "kernel": "lfsr_kernel<64>", "gbit_s": ni * nb / (ms3 * 1e-3) / 1e9,
+                             "roofline": {"bound": "alu",
+                                          "achieved_tops": ops / (ms3 * 1e-3) / 1e12,
+                                          "peak_tops": lop3_peak_tops(),
+                                          "frac": ops / (ms3 * 1e-3) / 1e12 / lop3_peak_tops()}},
     }), flush=True)
 
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <type_traits>
 
 #include "../../include/bitslice_lfsr.h"
@@ -16,6 +17,11 @@ using namespace mickey;
 namespace {
 
 constexpr int kLfsrThreads = 128;
+constexpr int kLfsrMaxSparseTaps = 16;  // at most this many taps: lfsr_sparse_kernel
+constexpr int kLfsrBlock = 64;                 // clocks per unrolled block of the sparse kernel
+constexpr int kLfsrSlots = kLfsrBlock + 64;    // its window: reads reach slot L - 1 + 63
+constexpr int kLfsrSparseThreads = 32;  // one warp per block: 1024 blocks even out over the SMs
+constexpr int kLfsrBatch = 8;           // clocks per batch of the sparse kernel
 
 struct LfsrMasks {
   uint32_t m[64];  // m[j] = a_{d-1-j} as 0 / ~0 (zero for j >= d)
@@ -64,18 +70,112 @@ __global__ void __launch_bounds__(kLfsrThreads)
     if (t < int(head)) out[uint64_t(t) * G + g] = t < 32 ? xlo[31 - t] : xhi[63 - t];
   const uint64_t clocks = n_bits - head;
   uint32_t *o = out + uint64_t(d) * G + g;
+  // blocks of W clocks whose chains run unguarded, so that the compiler may
+  // overlap the XOR chains of neighbouring clocks (only the newest term of a
+  // chain depends on the clock before); only the stores past the last
+  // requested clock are skipped, the extra clocks' words are discarded
+  const uint64_t blocks = (clocks + W - 1) / W;
 #pragma unroll 1
-  for (uint64_t c0 = 0; c0 < clocks; c0 += W) {
+  for (uint64_t b = 0; b < blocks; ++b) {
+    const uint64_t lim = clocks - b * W;  // >= 1
 #pragma unroll
     for (int u = 0; u < W; ++u) {
-      if (c0 + u < clocks) {
-        uint32_t f = y[(W - u) % W] & mk.m[0];
+      uint32_t f = y[(W - u) % W] & mk.m[0];
 #pragma unroll
-        for (int j = 1; j < W; ++j) f = lop3<0x78>(f, y[(j - u + W) % W], mk.m[j]);
-        y[(2 * W - 1 - u) % W] = f;
-        o[(c0 + u) * G] = f;
+      for (int j = 1; j < W; ++j) f = lop3<0x78>(f, y[(j - u + W) % W], mk.m[j]);
+      y[(2 * W - 1 - u) % W] = f;
+      if (uint64_t(u) < lim) o[uint64_t(u) * G] = f;
+    }
+    o += uint64_t(W) * G;
+  }
+}
+
+// Sparse taps: the recurrence s_{t+d} = XOR over the k taps j of s_{t+j}
+// costs k - 1 XORs per clock, not the d masked terms of the kernel above.
+// The tap positions are run-time values, and registers cannot be indexed at
+// run time, so each thread keeps its words in its own column of shared
+// memory: a window of L + 64 slots.  Clocks run in blocks of L = 64 (fully
+// unrolled, so every slot offset is an immediate): at the start of a block
+// slot s holds x_{c0+s} for s < d; clock u reads slots u + j and writes the
+// new word x_{c0+u+d} to slot u + d and, once u + d >= L, also to slot
+// u + d - L, where the next block reads it.  That second write lands on a
+// slot no later clock of the block reads (reads at clock u' >= u start at
+// slot u'), so the window never needs copying; it costs d / L extra stores
+// per clock.  Per clock and warp: k shared loads, 1 + d / L shared stores
+// and one global store, whose issue bounds the kernel.
+struct LfsrTaps {
+  uint32_t off[kLfsrMaxSparseTaps];  // tap positions j (a_j = 1), ascending
+};
+
+template <int K, int TB>
+__device__ __forceinline__ uint32_t lfsr_sparse_clock(const uint32_t *const (&rd)[K], int u) {
+  uint32_t f = rd[0][u * TB];
+#pragma unroll
+  for (int i = 1; i < K; ++i) f ^= rd[i][u * TB];
+  return f;
+}
+
+// B clocks per batch: the reads of a batch's clocks are all issued before
+// any of its writes, so their shared-memory latencies overlap.  Valid when
+// no read of a batch needs a word the same batch writes: the newest word a
+// clock reads is x_{c+j_max}, written d - j_max clocks earlier, so B <=
+// d - j_max.  B = 1 serves every tap set.
+template <int K, int TB, int B>
+__global__ void __launch_bounds__(TB)
+    lfsr_sparse_kernel(const uint64_t *seeds, size_t n, int d, LfsrTaps tp, uint64_t n_bits,
+                       uint32_t *out, uint32_t G) {
+  constexpr int L = kLfsrBlock;
+  extern __shared__ uint32_t lfsr_win[];  // kLfsrSlots x TB words
+  const uint32_t g = blockIdx.x * TB + threadIdx.x;
+  if (g >= G) return;  // threads use only their own column: no block-wide sync
+  uint32_t xlo[32], xhi[32];
+#pragma unroll
+  for (int l = 0; l < 32; ++l) {
+    const uint64_t i = uint64_t(g) * 32 + l;
+    const uint64_t v = i < n ? seeds[i] : 0ull;
+    xlo[31 - l] = uint32_t(v);
+    xhi[31 - l] = uint32_t(v >> 32);
+  }
+  transpose32(xlo);  // now xlo[31 - t] = word of bit t (t < 32), xhi[63 - t] (t >= 32)
+  transpose32(xhi);
+  uint32_t *col = lfsr_win + threadIdx.x;
+  const uint64_t head = n_bits < uint64_t(d) ? n_bits : uint64_t(d);
+#pragma unroll
+  for (int t = 0; t < 64; ++t) {
+    const uint32_t x = t < 32 ? xlo[31 - t] : xhi[63 - t];
+    if (t < d) col[t * TB] = x;
+    if (t < int(head)) out[uint64_t(t) * G + g] = x;
+  }
+  const uint64_t clocks = n_bits - head;
+  const uint32_t *rd[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) rd[i] = col + tp.off[i] * TB;
+  uint32_t *wr = col + d * TB;
+  uint32_t *o = out + uint64_t(d) * G + g;
+  const uint64_t full = clocks / L;
+#pragma unroll 1
+  for (uint64_t b = 0; b < full; ++b) {
+#pragma unroll
+    for (int u0 = 0; u0 < L; u0 += B) {
+      uint32_t f[B];
+#pragma unroll
+      for (int v = 0; v < B; ++v) f[v] = lfsr_sparse_clock<K, TB>(rd, u0 + v);
+#pragma unroll
+      for (int v = 0; v < B; ++v) {
+        const int u = u0 + v;
+        wr[u * TB] = f[v];
+        if (u + d >= L) wr[(u - L) * TB] = f[v];
+        o[uint64_t(u) * G] = f[v];
       }
     }
+    o += uint64_t(L) * G;
+  }
+#pragma unroll 1
+  for (int u = 0; u < int(clocks - full * L); ++u) {
+    const uint32_t f = lfsr_sparse_clock<K, TB>(rd, u);
+    wr[u * TB] = f;
+    if (u + d >= L) wr[(u - L) * TB] = f;
+    o[uint64_t(u) * G] = f;
   }
 }
 
@@ -422,6 +522,39 @@ CrcJoin crc_join_matrices(uint8_t poly) {
   return cj;
 }
 
+template <int K, int B>
+cudaError_t launch_lfsr_sparse_b(const uint64_t *seeds, size_t n, int d, const LfsrTaps &tp,
+                                 uint64_t n_bits, uint32_t *out, uint32_t G, cudaStream_t st) {
+  constexpr int TB = kLfsrSparseThreads;
+  const int smem = kLfsrSlots * TB * 4;
+  cudaError_t e = cudaFuncSetAttribute(lfsr_sparse_kernel<K, TB, B>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  lfsr_sparse_kernel<K, TB, B><<<(G + TB - 1) / TB, TB, smem, st>>>(seeds, n, d, tp, n_bits,
+                                                                     out, G);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_lfsr_sparse_k(const uint64_t *seeds, size_t n, int d, const LfsrTaps &tp,
+                                 uint64_t n_bits, uint32_t *out, uint32_t G, cudaStream_t st) {
+  const int j_max = int(tp.off[K - 1]);
+  if (d - j_max >= kLfsrBatch && !getenv("MICKEY_LFSR_NOBATCH"))
+    return launch_lfsr_sparse_b<K, kLfsrBatch>(seeds, n, d, tp, n_bits, out, G, st);
+  return launch_lfsr_sparse_b<K, 1>(seeds, n, d, tp, n_bits, out, G, st);
+}
+
+template <int K = 1>
+cudaError_t launch_lfsr_sparse(int k, const uint64_t *seeds, size_t n, int d, const LfsrTaps &tp,
+                               uint64_t n_bits, uint32_t *out, uint32_t G, cudaStream_t st) {
+  if constexpr (K > kLfsrMaxSparseTaps) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (k == K) return launch_lfsr_sparse_k<K>(seeds, n, d, tp, n_bits, out, G, st);
+    return launch_lfsr_sparse<K + 1>(k, seeds, n, d, tp, n_bits, out, G, st);
+  }
+}
+
 template <int W>
 cudaError_t launch_lfsr(const uint64_t *seeds, size_t n, int d, const LfsrMasks &mk,
                         uint64_t n_bits, uint32_t *out, uint32_t G, cudaStream_t st) {
@@ -457,9 +590,19 @@ MICKEY_API int mickey_lfsr_generate(const uint64_t *seeds, size_t n_inst, int de
       return set_error(MICKEY_E_CUDA, "seed upload");
     d_seeds = tmp;
   }
-  cudaError_t e = degree <= 16   ? launch_lfsr<16>(d_seeds, n_inst, degree, mk, n_bits, out, G, st)
-                  : degree <= 32 ? launch_lfsr<32>(d_seeds, n_inst, degree, mk, n_bits, out, G, st)
-                                 : launch_lfsr<64>(d_seeds, n_inst, degree, mk, n_bits, out, G, st);
+  int k = 0;
+  LfsrTaps tp{};
+  for (int j = 0; j < degree; ++j)
+    if ((taps >> j) & 1u) {
+      if (k < kLfsrMaxSparseTaps) tp.off[k] = uint32_t(j);
+      ++k;
+    }
+  const bool sparse = k <= kLfsrMaxSparseTaps && !getenv("MICKEY_LFSR_DENSE");
+  cudaError_t e =
+      sparse         ? launch_lfsr_sparse(k, d_seeds, n_inst, degree, tp, n_bits, out, G, st)
+      : degree <= 16 ? launch_lfsr<16>(d_seeds, n_inst, degree, mk, n_bits, out, G, st)
+      : degree <= 32 ? launch_lfsr<32>(d_seeds, n_inst, degree, mk, n_bits, out, G, st)
+                     : launch_lfsr<64>(d_seeds, n_inst, degree, mk, n_bits, out, G, st);
   if (tmp) cudaFreeAsync(tmp, st);
   if (e != cudaSuccess) return set_error(MICKEY_E_CUDA, "lfsr kernel launch");
   return set_error(MICKEY_OK, "");

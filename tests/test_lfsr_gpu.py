@@ -47,6 +47,43 @@ def test_lfsr_every_instance(d):
             assert np.array_equal(got[i], ref), (d, n_bits, i)
 
 
+def _sparse_taps(rng, d, k):
+    # a_0 = 1 plus k - 1 other distinct positions below d
+    others = rng.choice(np.arange(1, d), size=k - 1, replace=False) if k > 1 else []
+    t = 1
+    for j in others:
+        t |= 1 << int(j)
+    return t
+
+
+@pytest.mark.parametrize("d", [2, 5, 17, 33, 63, 64])
+def test_lfsr_sparse_and_dense_taps_every_instance(d, monkeypatch):
+    # up to 16 taps take the shared-memory kernel, more the mask kernel;
+    # lengths span several 64-clock blocks and a ragged remainder, and the
+    # same taps forced through the mask kernel give the same words
+    from paper_1909_04750_gb300.lfsr import lfsr_generate, unbitslice
+    rng = np.random.default_rng(100 + d)
+    n = 45
+    seeds = rng.integers(1, 1 << 62, n, dtype=np.uint64) & np.uint64((1 << d) - 1 if d < 64
+                                                                      else (1 << 64) - 1)
+    tap_sets = [_sparse_taps(rng, d, k) for k in sorted({1, 2, min(4, d), min(16, d),
+                                                          min(17, d), d})]
+    # low taps (newest tap at least 8 below the degree): the batched clocks
+    tap_sets += [t & ((1 << d) - 1) for t in (0b11011, 0b1000_0101, 0b11)] if d >= 16 else []
+    for taps in tap_sets:
+        for n_bits in (d + 1, 64 + d - 1, 5 * 64 + d + 13):
+            words = lfsr_generate(seeds, d, taps, n_bits)
+            got = unbitslice(words.cpu().numpy(), n)
+            for i in range(n):
+                ref = olfsr.lfsr_bits(int(seeds[i]), d, taps, n_bits)
+                assert np.array_equal(got[i], ref), (d, hex(taps), n_bits, i)
+            for env in ("MICKEY_LFSR_DENSE", "MICKEY_LFSR_NOBATCH"):
+                monkeypatch.setenv(env, "1")
+                other = lfsr_generate(seeds, d, taps, n_bits)
+                monkeypatch.delenv(env)
+                assert torch.equal(words, other), (env, d, hex(taps), n_bits)
+
+
 def test_lfsr_device_seeds_and_lane_padding():
     from paper_1909_04750_gb300.lfsr import lfsr_generate
     rng = np.random.default_rng(1)
