@@ -164,28 +164,31 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
 
 /* --------------------------------------------------------------------------
  * Launch configuration and autotuning of the keystream kernel (per layout).
- *   mode    MICKEY_MODE_GRID: one thread per 32-lane group, 4 warps per block;
- *           MICKEY_MODE_PERSISTENT: one clock warp per SM sub-partition,
- *           paired with an emission warp that transposes and stores its
- *           tiles, the groups x tiles work line cut into equal segments
- *           (used only when there are at least as many 1024-instance
- *           warp-groups as clock warps);
+ *   mode    MICKEY_MODE_GRID: one thread per 32-lane group, clocking and
+ *           emitting, 4 warps per block;
+ *           MICKEY_MODE_PERSISTENT: per SM sub-partition a clock warp paired
+ *           with an emission warp that transposes and stores its tiles; with
+ *           at least as many 1024-instance warp-groups as clock warps the
+ *           groups x tiles work line is cut into equal segments (one block
+ *           per SM, cooperative), else each pair takes one whole warp-group;
  *           MICKEY_MODE_PERSISTENT2: two warps per SM sub-partition, each
  *           clocking and emitting (two blocks per SM, rows staged four
- *           tiles deep);
- *           MICKEY_MODE_AUTO: persistent whenever there are at least as
- *           many warp-groups as clock warps, else grid.
+ *           tiles deep; with too few warp-groups it runs as PERSISTENT);
+ *           MICKEY_MODE_AUTO: as PERSISTENT.
  *   unroll  clocks per inner step, 2 or 4.
- *   stage   row layouts: stage four 32-bit words per row in shared memory
- *           and write 16-byte chunks (needs n_bits % 128 == 0).
+ *   stage   row layouts: stage each row's words of several tiles in shared
+ *           memory and write 16- or 32-byte chunks (four tiles for GRID and
+ *           PERSISTENT2, eight for PERSISTENT; used when n_bits is a multiple
+ *           of 32 x that depth and the output 16-byte aligned).
  * Environment, read when a handle is created: MICKEY_MODE (grid,
  * persistent, persistent2), MICKEY_UNROLL (2, 4), MICKEY_STAGE (0, 1) and
  * MICKEY_PERSIST_BLOCKS (fewer persistent blocks than SMs) set the defaults;
  * MICKEY_SPIN_LIMIT bounds a persistent tail piece's wait for its head
  * (polls of about 256 ns, default 2^24), after which mickey_sync reports
- * MICKEY_E_TIMEOUT and that call's output and state are undefined; MICKEY_TEST_UNPUBLISHED=1 is a test
- * hook that makes every such wait run out (tails wait for a value no head
- * writes), to exercise that path without a fault.
+ * MICKEY_E_TIMEOUT and that call's output and state are undefined;
+ * MICKEY_TEST_UNPUBLISHED=1 is a test hook that makes every such wait run
+ * out (tails wait for a value no head writes), to exercise that path
+ * without a fault.
  * ------------------------------------------------------------------------ */
 #define MICKEY_MODE_AUTO 0
 #define MICKEY_MODE_GRID 1

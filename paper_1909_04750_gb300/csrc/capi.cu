@@ -227,52 +227,60 @@ int check_generate(const mickey_streams *s, uint64_t n_bits, const void *out, in
   return check_limit(s, n_bits);
 }
 
-bool is_persistent(int mode) {
-  return mode == MICKEY_MODE_PERSISTENT || mode == MICKEY_MODE_PERSISTENT2;
-}
-
 // Blocks per SM of a persistent launch in `mode`.
 uint32_t persist_per_sm(int mode) { return mode == MICKEY_MODE_PERSISTENT2 ? 2u : 1u; }
 
-// Whether a launch should use a persistent kernel: whenever there are at
-// least as many warp-groups as clock warps.  With its clock warps relieved
-// of the emission, the one-block-per-SM persistent launch outruns the grid
-// launch at every size measured (2^20 to 2^24 instances), so AUTO takes it.
+// Whether a launch can use a persistent kernel of `mode`: there must be at
+// least as many warp-groups as warps that clock.
 bool use_persistent(const mickey_streams *s, int mode) {
   const uint64_t W = (s->G + 31) / 32;
   const uint64_t slots = uint64_t(s->persist_blocks) * persist_per_sm(mode) * 4;
-  if (mode == MICKEY_MODE_GRID || W < slots) return false;
-  return true;
+  return mode != MICKEY_MODE_GRID && W >= slots;
 }
 
 // One keystream launch of `bits` clocks into a device buffer.
+//   GRID                      one thread per group, clocking and emitting
+//   PERSISTENT2, enough groups two clocking warps per SM sub-partition
+//   otherwise (AUTO, PERSISTENT) the paired kernel: clock warps beside emission
+//                             warps; with enough warp-groups the cooperative
+//                             launch with equal segments, else one warp-group
+//                             per pair.  It outruns the others at every size
+//                             measured, so AUTO takes it.
 int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
   KeystreamArgs ka{s->d_state, s->G, s->Gpad, s->n, bits, out};
   const auto &c = s->cfg[layout];
-  const int mode = c.set ? c.mode : s->mode;
+  int mode = c.set ? c.mode : s->mode;
   const int unroll = c.set ? c.unroll : s->unroll;
   const bool stage = c.set ? c.stage : s->stage;
-  if (use_persistent(s, mode)) {
-    const uint32_t per_sm = persist_per_sm(mode);
-    const uint64_t W = (s->G + 31) / 32, slots = uint64_t(s->persist_blocks) * per_sm * 4;
-    const uint64_t NT = (bits + 31) / 32;
-    PersistArgs pa;
-    pa.blocks = uint32_t(s->persist_blocks) * per_sm;
-    pa.stage_tiles = per_sm == 2 ? 4u : 8u;
-    pa.W = uint32_t(W);
-    pa.L = (W * NT + slots - 1) / slots;
-    pa.flags = s->d_flags;
-    s->epoch = s->epoch % 0x7fffffffu + 1;   // 1 .. 2^31 - 1 (0 is the flags' initial value)
-    pa.epoch = s->epoch;
-    pa.wait_epoch = s->test_unpublished ? (s->epoch | 0x80000000u) : s->epoch;
-    pa.spin_limit = s->spin_limit;
-    pa.err = s->d_err;
-    CUDA_TRY(launch_keystream(ka, layout, unroll, stage, &pa, s->stream),
-             "keystream_persistent_kernel launch");
-  } else {
+  if (mode == MICKEY_MODE_GRID) {
     CUDA_TRY(launch_keystream(ka, layout, unroll, stage, nullptr, s->stream),
              "keystream_kernel launch");
+    return MICKEY_OK;
   }
+  if (mode == MICKEY_MODE_PERSISTENT2 && !use_persistent(s, mode)) mode = MICKEY_MODE_PERSISTENT;
+  const uint32_t per_sm = persist_per_sm(mode);
+  const uint64_t W = (s->G + 31) / 32, NT = (bits + 31) / 32;
+  PersistArgs pa;
+  pa.stage_tiles = per_sm == 2 ? 4u : 8u;
+  pa.W = uint32_t(W);
+  if (use_persistent(s, mode)) {
+    const uint64_t slots = uint64_t(s->persist_blocks) * per_sm * 4;
+    pa.blocks = uint32_t(s->persist_blocks) * per_sm;
+    pa.cooperative = 1;
+    pa.L = (W * NT + slots - 1) / slots;
+  } else {  // one warp-group per clock/emission pair, four pairs per block
+    pa.blocks = uint32_t((W + 3) / 4);
+    pa.cooperative = 0;
+    pa.L = NT;
+  }
+  pa.flags = s->d_flags;
+  s->epoch = s->epoch % 0x7fffffffu + 1;   // 1 .. 2^31 - 1 (0 is the flags' initial value)
+  pa.epoch = s->epoch;
+  pa.wait_epoch = s->test_unpublished ? (s->epoch | 0x80000000u) : s->epoch;
+  pa.spin_limit = s->spin_limit;
+  pa.err = s->d_err;
+  CUDA_TRY(launch_keystream(ka, layout, unroll, stage, &pa, s->stream),
+           "keystream persistent launch");
   return MICKEY_OK;
 }
 
@@ -571,8 +579,7 @@ int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout, mickey_tune_resu
   float best_ms = 1e30f;
   mickey_streams::LayoutCfg best = keep;
   for (int mode : {MICKEY_MODE_GRID, MICKEY_MODE_PERSISTENT, MICKEY_MODE_PERSISTENT2}) {
-    if (is_persistent(mode) && W < uint64_t(s->persist_blocks) * persist_per_sm(mode) * 4)
-      continue;
+    if (mode == MICKEY_MODE_PERSISTENT2 && !use_persistent(s, mode)) continue;
     for (int unroll : kUnrolls) {
       for (int stage = 0; stage <= (row && n_bits % 128 == 0 ? 1 : 0); ++stage) {
         auto &c = s->cfg[layout];

@@ -76,7 +76,9 @@ constexpr int kKsThreads = 128;
 // Persistent mode (see keystream_persistent_kernel): W warp-groups, L tiles
 // per warp, one flag word per warp-group (compared with `epoch`).
 struct PersistArgs {
-  uint32_t blocks;      // cooperative grid: 1 or 2 blocks of kKsThreads per SM
+  uint32_t blocks;      // grid: 1 or 2 blocks per SM (cooperative), or one block per
+                        // 4 warp-groups (paired launch with L = NT, not cooperative)
+  uint32_t cooperative; // 1: all blocks resident (needed when segments hand off)
   uint32_t stage_tiles; // row staging depth: 8 (one block per SM) or 4 (two)
   uint32_t W;           // warp-groups = ceil(G / 32)
   uint64_t L;           // tiles of the work line per warp

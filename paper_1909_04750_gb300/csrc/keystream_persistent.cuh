@@ -202,7 +202,10 @@ __device__ __forceinline__ void emit_piece(const KeystreamArgs &a, EmitCtx e, ui
 // and meet once per tile at named barrier 1 + w, the tile buffers
 // alternating between them.  The hand-off of a tail piece is the clock
 // warp's; when its wait runs out it raises the error flag and clocks the
-// piece anyway, so both warps still meet the same number of times.
+// piece anyway, so both warps still meet the same number of times.  With
+// fewer warp-groups than clock warps the same kernel runs one whole
+// warp-group per pair (L = NT, no pieces to hand off), launched without the
+// cooperative attribute.
 template <int LAYOUT, int U, int ST>
 __global__ void __launch_bounds__(2 * kKsThreads, 1)
     keystream_ws_kernel(KeystreamArgs a, EmitCtx e, PersistArgs p) {
@@ -258,7 +261,7 @@ cudaError_t launch_ws_kernel(const KeystreamArgs &a, const EmitCtx &e, const Per
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
+  attr[0].val.cooperative = p.cooperative ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, keystream_ws_kernel<LAYOUT, U, ST>, a, e, p);
