@@ -190,6 +190,27 @@ def test_lane_independence():
     assert changed.tolist() == [37]
 
 
+def test_rejected_calls_leave_the_streams_untouched():
+    # host-side argument errors (no bits, a 32-bit layout that cannot hold
+    # n_bits, an unknown layout) return before any launch: positions stay,
+    # and the next call continues exactly where the streams stood
+    import ctypes
+    s = workloads.plain_scale(40)
+    st = _streams(s)
+    first = st.generate(64, "bytes").cpu().numpy()
+    L = N.lib()
+    buf = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    assert L.mickey_generate(st._h, 0, p, N.LAYOUT_BYTES) == N.E_ARG
+    assert L.mickey_generate(st._h, 40, p, N.LAYOUT_U32) == N.E_LAYOUT
+    assert L.mickey_generate(st._h, 64, p, 7) == N.E_LAYOUT
+    assert st.position(0) == 64
+    rest = st.generate(64, "bytes").cpu().numpy()
+    st.sync()
+    ref = _ref(s, 128)
+    assert np.array_equal(first, ref[:, :8]) and np.array_equal(rest, ref[:, 8:16])
+
+
 def test_device_iv_len_above_80_reported():
     from paper_1909_04750_gb300.streams import Streams
     s = workloads.plain_scale(40)
