@@ -244,9 +244,15 @@ def _sample_rows(n, k, seed):
 
 
 def test_plain_scale_full_size_sampled():
+    # in the launch configurations bench.py times: the autotuner's choice
+    # for this shape, per layout
+    from paper_1909_04750_gb300 import autotune
     s = workloads.plain_scale()
     n_bits = int(s.n_bits[0])
     st = _streams(s)
+    autotune.tune(st, n_bits, N.LAYOUT_BYTES)
+    autotune.tune(st, n_bits, N.LAYOUT_BITSLICED_U32)
+    assert st.position(0) == 0
     out = st.generate(n_bits, "bytes")
     st.reset(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
     bs = st.generate(n_bits, "bitsliced")
@@ -273,9 +279,11 @@ def test_plain_scale_full_size_sampled():
 
 
 def test_fused_full_size_sampled():
+    from paper_1909_04750_gb300 import autotune
     s = workloads.fused()
     n_bits = int(s.n_bits[0])
     st = _streams(s)
+    autotune.tune(st, n_bits, N.LAYOUT_U32_F32)     # the launch bench_fused times
     both = st.generate(n_bits, "u32_f32")
     st.sync()
     u = both[0]
