@@ -341,6 +341,31 @@ def test_persistent_mode_matches_grid_and_oracle(monkeypatch, n, n_bits, blocks,
         assert np.array_equal(got["u32_f32"][1][rows].view(np.float32), oracle.to_f32(u))
 
 
+@pytest.mark.parametrize("n,n_bits", [(5 * 1024 - 7, 1000), (33, 4096), (300 * 1024, 256)])
+def test_paired_kernel_with_few_warp_groups_matches_grid(monkeypatch, n, n_bits):
+    # fewer warp-groups than clock warps: each clock/emission pair takes a
+    # whole warp-group (no segments, no hand-off); compared with the grid
+    # kernel word for word and with the oracle on sampled rows
+    s = workloads.plain_scale(n)
+    monkeypatch.setenv("MICKEY_MODE", "grid")
+    st_g = _streams(s)
+    monkeypatch.setenv("MICKEY_MODE", "persistent")
+    st_p = _streams(s)
+    for layout in ("bytes", "bitsliced", "u32_f32"):
+        if layout == "u32_f32" and n_bits % 32:
+            continue
+        a = st_g.generate(n_bits, layout).cpu().numpy()
+        b = st_p.generate(n_bits, layout).cpu().numpy()
+        st_p.sync()
+        assert np.array_equal(a, b), layout
+    calls = 2 + (n_bits % 32 == 0)             # generate calls made so far
+    rows = _sample_rows(n, 48, 17)
+    ref = _ref(s.subset(rows), (calls + 1) * n_bits)
+    last = st_p.generate(n_bits, "bytes").cpu().numpy()
+    st_p.sync()
+    assert np.array_equal(last[rows], ref[:, calls * n_bits // 8:])
+
+
 def test_autotune_keeps_positions_and_output():
     from paper_1909_04750_gb300 import autotune
     s = workloads.plain_scale(24 * 1024)
