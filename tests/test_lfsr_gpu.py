@@ -133,3 +133,23 @@ def test_crc8_full_size_sampled():
     rows = data[torch.from_numpy(pick).cuda()].cpu().numpy()
     ref = olfsr.crc8_batch(rows, 0x1D, 0xFF, 0xFF, threads=THREADS)
     assert np.array_equal(got[pick], ref)
+
+
+def test_lfsr_full_size_sampled(monkeypatch):
+    # the measured workload: 2^20 LFSRs of degree 64 with the taps of
+    # x^64 + x^4 + x^3 + x + 1, 4096 bits each, through the few-tap kernel
+    # (checked on sampled instances) and the mask kernel (same words)
+    from paper_1909_04750_gb300.lfsr import lfsr_generate
+    n, nb, d, taps = 1 << 20, 4096, 64, 0b11011
+    g = torch.Generator(device="cuda").manual_seed(5)
+    seeds = torch.randint(1, 1 << 62, (n,), dtype=torch.int64, device="cuda", generator=g)
+    words = lfsr_generate(seeds, d, taps, nb)
+    rng = np.random.default_rng(3)
+    pick = np.unique(np.concatenate([[0, 31, 32, n - 1], rng.integers(0, n, 64)]))
+    sd = seeds.cpu().numpy().view(np.uint64)
+    w = words.cpu().numpy().view(np.uint32)                 # [nb, G]
+    for i in pick:
+        got = ((w[:, i // 32] >> np.uint32(i % 32)) & 1).astype(np.uint8)
+        assert np.array_equal(got, olfsr.lfsr_bits(int(sd[i]), d, taps, nb)), int(i)
+    monkeypatch.setenv("MICKEY_LFSR_DENSE", "1")
+    assert torch.equal(words, lfsr_generate(seeds, d, taps, nb))
