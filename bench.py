@@ -15,9 +15,7 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
-import tempfile
 import time
 
 import numpy as np
@@ -29,12 +27,10 @@ METRIC = "keystream Gbit/s on 1 GB300 (bit-exact), % of int-LOP roofline; served
 WORKLOAD = ("plain_scale: 2^20 MICKEY 2.0 instances (32768 bitsliced groups), 80-bit keys "
             "and IVs from splitmix64 seed 2, 100 mixing preclocks, 2^14 keystream bits "
             "per instance, row-major bytes output (2 GiB)")
-# Integer-logic peak of the GB300: 152 SMs x 64 LOP3 results per SM per
-# clock (measured with mickey_probe_lop3: 63.2-64.0 per SM-cycle over 1-8
-# resident blocks) x the maximum SM clock of 2070 MHz = 20.14 T ops/s.
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-LOP3_PER_SM_CLK = 64.0
+# The integer-logic roofline is measured in the same process: SM count from
+# the device, LOP3 results per SM per SM-cycle from mickey_probe_lop3 (run
+# before the timed region), at the maximum SM clock and at the median clock
+# sampled during the timed region.
 
 # DRAM traffic of one keystream launch of the plain workload at scale
 # (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu capture of the
@@ -56,64 +52,11 @@ def parse():
     p.add_argument("--n-bits", type=int, default=1 << 14)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the fused, batched and served workloads")
+    p.add_argument("--served-duration", type=float, default=30.0)
+    p.add_argument("--verify-rows", type=int, default=1024)
     return p.parse_args()
-
-
-class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
-
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.path = None
-
-    def start(self):
-        try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.f, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
-
-    def stop(self):
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        if self.proc is None:
-            return out
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
-        os.unlink(self.path)
-        if not rows:
-            return out
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in rows:
-            for k, name in enumerate(names):
-                if r[5 + k].lower().startswith("active"):
-                    reasons.add(name)
-        load = [x for x in sm if x > 0.5 * (max(sm) if sm else 1)]
-        out.update(sm_mhz=statistics.median(load) if load else None,
-                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
-                   samples=len(rows))
-        return out
 
 
 def cpu_baseline(n_bits: int, seconds: float = 3.0):
@@ -177,6 +120,102 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+# ------------------------------------------------------------------ checks
+# Sampled comparisons of timed outputs with the scalar oracle, run after the
+# timed regions.  A mismatch is reported in the line and fails the run.
+
+def _sample_rows(n: int, k: int, seed: int = 12345) -> np.ndarray:
+    """k row indices of n: the first and the last 32-lane group, and random
+    rows in between."""
+    fixed = np.concatenate([np.arange(min(32, n)), np.arange(max(0, n - 32), n)])
+    rng = np.random.default_rng(seed)
+    extra = rng.choice(n, size=min(n, max(0, k - fixed.size)), replace=False)
+    return np.unique(np.concatenate([fixed, extra]))
+
+
+def verify_rows(s, out, n_bits: int, k: int) -> dict:
+    """Rows of a row-major bytes output against the oracle."""
+    import oracle
+    import torch
+    idx = _sample_rows(s.n, k)
+    got = out[torch.from_numpy(idx).to(out.device)].cpu().numpy()
+    ref = oracle.batch_bytes(s.keys[idx], s.ivs[idx], s.iv_lens[idx], n_bits,
+                             threads=os.cpu_count() or 1)
+    return {"rows": int(idx.size), "ok": bool(np.array_equal(got, ref)),
+            "what": "row-major bytes of sampled instances (first and last group included) of "
+                    "the last timed step == scalar oracle"}
+
+
+def verify_fused(s, out, n_bits: int = 1 << 12, k: int = 1024) -> dict:
+    import oracle
+    import torch
+    idx = _sample_rows(s.n, k)
+    sel = torch.from_numpy(idx).to(out.device)
+    got_u = out[0][sel].cpu().numpy().view(np.uint32)
+    got_f = out[1][sel].cpu().numpy().view(np.float32)
+    ref = oracle.batch_bytes(s.keys[idx], s.ivs[idx], s.iv_lens[idx], n_bits,
+                             threads=os.cpu_count() or 1)
+    ref_u = oracle.to_u32(ref, n_bits)
+    ok = np.array_equal(got_u, ref_u) and np.array_equal(got_f, oracle.to_f32(ref_u))
+    return {"rows": int(idx.size), "ok": bool(ok),
+            "what": "u32 words and FP32 uniforms of sampled instances (first and last group "
+                    "included) of the last timed step == scalar oracle"}
+
+
+def verify_batched(s, b, out) -> dict:
+    """Sampled streams of the last replay: the 4 longest, the 4 shortest, 8 of
+    every IV length, 48 more at random."""
+    import oracle
+    n = s.n
+    order = np.argsort(s.n_bits, kind="stable")
+    rng = np.random.default_rng(7)
+    pick = [order[-4:], order[:4], rng.choice(n, 48, replace=False)]
+    for L in np.unique(s.iv_lens):
+        cand = np.flatnonzero(s.iv_lens == L)
+        pick.append(rng.choice(cand, min(8, cand.size), replace=False))
+    idx = np.unique(np.concatenate(pick))
+    ref = oracle.batch_bytes(s.keys[idx], s.ivs[idx], s.iv_lens[idx], s.n_bits[idx],
+                             threads=os.cpu_count() or 1)
+    host = out.cpu().numpy()
+    ok = True
+    for j, i in enumerate(idx):
+        o, nb = int(b.offsets[i]), (int(s.n_bits[i]) + 7) // 8
+        ok &= np.array_equal(host[o:o + nb], np.asarray(ref[j]).reshape(-1))
+    return {"streams": int(idx.size), "ok": bool(ok),
+            "bits": int(s.n_bits[idx].sum()),
+            "what": "whole keystreams of sampled streams (longest, shortest, every IV length) "
+                    "of the last replay == scalar oracle"}
+
+
+def verify_served(srv, reqs, keyset, k: int = 96, max_bits: int = 1 << 21) -> dict:
+    """Resident states after the run of sampled streams (those whose
+    requests total at most max_bits, several with more than one request)
+    against the oracle's state after the same number of keystream bits."""
+    import oracle
+    total, count = {}, {}
+    for r in reqs:
+        total[r.stream_id] = total.get(r.stream_id, 0) + 8 * r.n_bytes
+        count[r.stream_id] = count.get(r.stream_id, 0) + 1
+    small = [sid for sid, b in total.items() if b <= max_bits]
+    multi = [sid for sid in small if count[sid] > 1]
+    rng = np.random.default_rng(11)
+    ids = sorted(set(multi[: k // 2]) | set(rng.choice(small, min(len(small), k // 2),
+                                                       replace=False).tolist()))
+    got = srv.read_states(np.array(ids, np.uint32))
+    ok = True
+    for j, sid in enumerate(ids):
+        st = oracle.init(keyset.keys[sid].tobytes(), keyset.ivs[sid].tobytes(),
+                         int(keyset.iv_lens[sid]))
+        oracle.keystream_from(st, total[sid])
+        r, s_ = st.bits()
+        rec = np.unpackbits(got[j])
+        ok &= np.array_equal(rec[:100], r) and np.array_equal(rec[104:204], s_)
+    return {"streams": len(ids), "with_several_requests": int(sum(count[i] > 1 for i in ids)),
+            "ok": bool(ok),
+            "what": "resident state after every request of sampled streams == scalar oracle "
+                    "state after the same keystream bits"}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -190,8 +229,10 @@ def main():
     import torch.distributed as dist
 
     from paper_1909_04750_gb300 import _native as N
-    from paper_1909_04750_gb300 import autotune, shard, workloads
+    from paper_1909_04750_gb300 import autotune, shard
+    from paper_1909_04750_gb300 import peak as P
     from paper_1909_04750_gb300.build import build, sources_digest
+    from paper_1909_04750_gb300.clocks import ClockSampler
     from paper_1909_04750_gb300.streams import Streams, ops_per_clock
 
     torch.cuda.set_device(local)
@@ -217,6 +258,8 @@ def main():
     # launch configuration from the autotuner (timed once per shape, cached)
     tuned = autotune.tune(st, n_bits, N.LAYOUT_BYTES)
     tuned_bs = autotune.tune(st, n_bits, N.LAYOUT_BITSLICED_U32)
+    # the roofline's factors, measured on this device before the timed region
+    pk = P.measure()
 
     def step(layout="bytes", o=out):
         st.reset(keys, ivs, lens)
@@ -227,8 +270,7 @@ def main():
     torch.cuda.synchronize()
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    sampler = ClockSampler(local)
-    sampler.start()
+    sampler = ClockSampler(local).start()
     shard.barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
@@ -244,9 +286,12 @@ def main():
     st.sync()
     step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
     ks_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    init_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     total_ms = shard.max_over_ranks(sum(step_ms))
     bits_per_step = n * n_bits * world
     value = bits_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    # the last timed step's output against the oracle (every rank its own shard)
+    verified = verify_rows(s, out, n_bits, args.verify_rows)
 
     # secondary: bitsliced-u32 layout, same step otherwise
     out_bs = torch.empty(((n + 31) // 32, n_bits), dtype=torch.int32, device="cuda")
@@ -269,7 +314,9 @@ def main():
     ops = groups * n_bits * ops_per_clock(False)
     ks_avg_s = statistics.mean(ks_ms) * 1e-3
     achieved = ops / ks_avg_s / 1e12
-    peak = N_SM * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    sm_max = clocks.get("sm_max_mhz") or P.max_sm_mhz(local) or pk["probe_sm_mhz"]
+    peak = P.peak_tops(pk, sm_max)
+    peak_med = P.peak_tops(pk, clocks["sm_mhz"]) if clocks.get("sm_mhz") else None
     init_ops = groups * 260 * ops_per_clock(True)
     whole_ops = ops + init_ops
     alg_bytes = n * n_bits // 8 + 2 * groups * 200 * 4        # output + state in and out
@@ -284,10 +331,10 @@ def main():
     if not args.no_e2e:
         host_out = torch.empty((n, n_bits // 8), dtype=torch.uint8, pin_memory=True)
         # the step's inputs live in pinned host memory (copied in every step)
-        pk = torch.from_numpy(s.keys).pin_memory()
+        pk_ = torch.from_numpy(s.keys).pin_memory()
         pv = torch.from_numpy(s.ivs).pin_memory()
         pl = torch.from_numpy(s.iv_lens.astype(np.uint32).view(np.int32)).pin_memory()
-        hk, hv, hl = pk.numpy(), pv.numpy(), pl.numpy().view(np.uint32)
+        hk, hv, hl = pk_.numpy(), pv.numpy(), pl.numpy().view(np.uint32)
 
         h = Streams(hk, hv, hl)            # host-memory inputs
 
@@ -307,6 +354,19 @@ def main():
                "d2h_bytes_per_step": int(host_out.numel()) * world}
         h.free()
         del host_out
+    st.free()
+    del out, flush
+    torch.cuda.empty_cache()
+
+    # the other workloads (one GPU only: they would hold every GPU of a
+    # multi-GPU run for minutes)
+    extras = {}
+    if world == 1 and not args.no_extras:
+        from paper_1909_04750_gb300 import bench_batched, bench_fused, bench_served
+        extras["fused"] = bench_fused.measure(peak=pk, verify=verify_fused)
+        extras["batched"] = bench_batched.measure(plain_gbit_s=value, verify=verify_batched)
+        extras["served"] = bench_served.measure(duration=args.served_duration,
+                                                plain_gbit_s=value, verify=verify_served)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -326,21 +386,32 @@ def main():
                                     / peak,
             "bitsliced_u32_gbit_s": bs_value,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
+                         "unit": "Tops/s", "frac": achieved / peak,
+                         "peak_at_median_clock": peak_med,
+                         "frac_at_median_clock": achieved / peak_med if peak_med else None,
+                         "traffic": traffic,
                          "traffic_unit": "bytes per launch", "algorithmic_bytes": alg_bytes,
                          "kernel": "keystream kernel, bytes layout (%s)" % autotune.describe(tuned),
                          "ops_per_clock_per_group": ops_per_clock(False),
-                         "peak_basis": "%d SMs x %g LOP3/SM/clk (mickey_probe_lop3) x %g MHz"
-                                       % (N_SM, LOP3_PER_SM_CLK, SM_MAX_MHZ)},
+                         "init_frac": init_ops / (statistics.mean(init_ms) * 1e-3) / 1e12 / peak,
+                         "peak_basis": "%d SMs (device) x %.2f LOP3/SM/clk (mickey_probe_lop3, "
+                                       "this process) x %g MHz (max SM clock)"
+                                       % (pk["n_sm"], pk["lop3_per_sm_clk"], sm_max)},
+            "verified": verified,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
+            **extras,
         }
         print(json.dumps(line), flush=True)
-    st.free()
     if world > 1:
         dist.destroy_process_group()
+    bad = [k for k, v in [("plain", verified)] + [(k, e.get("verified")) for k, e in
+                                                    extras.items()] if v and not v["ok"]]
+    if bad:
+        print("bench: output differs from the oracle in: %s" % ", ".join(bad), file=sys.stderr)
+        sys.exit(1)
 
 
 if __name__ == "__main__":

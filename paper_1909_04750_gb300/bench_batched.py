@@ -18,6 +18,7 @@ which the critical path of a single batch does not bound.
 """
 import argparse
 import json
+import statistics
 
 import numpy as np
 import torch
@@ -25,6 +26,7 @@ import torch
 from . import workloads
 from .batch import Batch, tune
 from .build import build
+from .clocks import ClockSampler
 from .streams import Streams
 
 
@@ -60,20 +62,12 @@ def lone_group_ns_per_clock(n_bits: int = 1 << 16) -> float:
     return e0.elapsed_time(e1) * 1e6 / n_bits
 
 
-def main():
-    p = argparse.ArgumentParser()
-    p.add_argument("--runs", type=int, default=3)
-    p.add_argument("--n", type=int, default=workloads.BATCHED["n"])
-    p.add_argument("--plain-gbit-s", type=float, default=None,
-                   help="plain-workload throughput for the work bound (measured if absent)")
-    p.add_argument("--steady", type=int, default=0, help="batches for the steady-state rate")
-    p.add_argument("--pipeline", type=int, default=4, help="handles (CUDA streams) in flight")
-    p.add_argument("--steady-split", type=int, default=0,
-                   help="split threshold for the steady-state run as max_clocks / this "
-                        "(0: the tuned one)")
-    a = p.parse_args()
-    build()
-    s = workloads.batched(a.n)
+def measure(runs: int = 3, n: int = workloads.BATCHED["n"], steady: int = 12,
+            pipeline: int = 4, steady_split: int = 0, plain_gbit_s=None, verify=None) -> dict:
+    """Time one replay of the batched workload `runs` times (and, with
+    `steady`, batches back to back); `verify(streamset, batch, out)` checks
+    the last replay's output and returns a dict for the line."""
+    s = workloads.batched(n)
     keys, ivs = torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda()
     b = Batch(s.n_bits, s.iv_lens)
     out = torch.empty(b.output_bytes, dtype=torch.uint8, device="cuda")
@@ -82,13 +76,15 @@ def main():
     b.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
-    for _ in range(a.runs):
+    sampler = ClockSampler(torch.cuda.current_device()).start()
+    for _ in range(runs):
         e0.record(b.stream)
         b.run(keys, ivs, out)
         e1.record(b.stream)
         b.sync()
         times.append(e0.elapsed_time(e1))
-    ms = min(times)
+    clocks = sampler.stop()
+    ms = statistics.mean(times)
     bits = int(s.n_bits.sum())
     t_thread = lone_group_ns_per_clock()
     t_clk = lone_split_ns_per_clock()
@@ -96,31 +92,63 @@ def main():
     line = {
         "metric": "batched keystream Gbit/s (100k ragged streams, one persistent launch)",
         "value": bits / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "ms_per_run": ms,
-        "runs": a.runs, "streams": b.n, "keystream_bits": bits,
+        "ms_runs": times, "runs": runs, "streams": b.n, "keystream_bits": bits,
         "groups_clocks_total": b.total_clocks, "longest_group_clocks": b.max_clocks,
         "lone_split_ns_per_clock": t_clk, "lone_thread_group_ns_per_clock": t_thread,
         "critical_path_ms": crit_ms, "frac_of_critical_path": crit_ms / ms,
-        "config": {"unroll": tuned["unroll"], "blocks_per_sm": tuned["blocks_per_sm"],
+        "bound": "critical path: the longest group's clocks one after another",
+        "config": {"workload": "batched: 100,000 streams, lengths log-uniform in "
+                               "[2^10, 2^22] bits, IV lengths {0,16,...,80}, seed 3",
+                   "unroll": tuned["unroll"], "blocks_per_sm": tuned["blocks_per_sm"],
                    "split_clocks": tuned["split_clocks"],
                    "split_groups": tuned.get("split_groups")},
+        "clocks": clocks,
     }
-    if a.plain_gbit_s:
-        line["work_bound_ms"] = bits / (a.plain_gbit_s * 1e9) * 1e3
-    if a.steady:
+    if plain_gbit_s:
+        line["work_bound_ms"] = bits / (plain_gbit_s * 1e9) * 1e3
+        line["vs_plain"] = line["value"] / plain_gbit_s
+    if verify is not None:
+        line["verified"] = verify(s, b, out)
+    if steady:
         cfg = dict(tuned)
-        if a.steady_split:
-            cfg["split_clocks"] = b.max_clocks // a.steady_split
-        line["steady"] = steady_state(b, s, keys, ivs, cfg, a.steady, a.pipeline)
+        if steady_split:
+            cfg["split_clocks"] = b.max_clocks // steady_split
+        b.free()
+        del out
+        torch.cuda.empty_cache()
+        sampler = ClockSampler(torch.cuda.current_device()).start()
+        line["steady"] = steady_state(b, s, keys, ivs, cfg, steady, pipeline)
+        line["steady"]["clocks"] = sampler.stop()
         line["steady"]["split_clocks"] = cfg["split_clocks"]
-    print(json.dumps(line), flush=True)
-    b.free()
+        if plain_gbit_s:
+            line["steady"]["vs_plain"] = line["steady"]["gbit_s"] / plain_gbit_s
+    else:
+        b.free()
+    return line
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--runs", type=int, default=3)
+    p.add_argument("--n", type=int, default=workloads.BATCHED["n"])
+    p.add_argument("--plain-gbit-s", type=float, default=None,
+                   help="plain-workload throughput for the work bound")
+    p.add_argument("--steady", type=int, default=0, help="batches for the steady-state rate")
+    p.add_argument("--pipeline", type=int, default=4, help="handles (CUDA streams) in flight")
+    p.add_argument("--steady-split", type=int, default=0,
+                   help="split threshold for the steady-state run as max_clocks / this "
+                        "(0: the tuned one)")
+    a = p.parse_args()
+    build()
+    print(json.dumps(measure(a.runs, a.n, a.steady, a.pipeline, a.steady_split,
+                             a.plain_gbit_s)), flush=True)
 
 
 def steady_state(b0, s, keys, ivs, tuned, k: int, pipeline: int) -> dict:
     """K batches back to back over `pipeline` handles on their own streams."""
     streams = [torch.cuda.Stream() for _ in range(pipeline)]
     hs = [Batch(s.n_bits, s.iv_lens, stream=st) for st in streams]
-    outs = [torch.empty(b0.output_bytes, dtype=torch.uint8, device="cuda") for _ in hs]
+    outs = [torch.empty(hs[0].output_bytes, dtype=torch.uint8, device="cuda") for _ in hs]
     for h, o in zip(hs, outs):
         h.set_config(tuned["unroll"], tuned["blocks_per_sm"], tuned["split_clocks"])
         h.run(keys, ivs, o)                              # capture + warm-up

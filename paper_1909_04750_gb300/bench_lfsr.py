@@ -20,7 +20,7 @@ import torch
 
 from . import lfsr
 from .build import build
-from .peak import lop3_peak_tops
+from . import peak as P
 
 
 def _hbm_peak_gbs() -> float | None:
@@ -72,6 +72,8 @@ def main():
     finally:
         del os.environ["MICKEY_LFSR_DENSE"]
     ops = (ni // 32) * (nb - d) * 64
+    pk = P.measure()
+    peak = P.peak_tops(pk, P.max_sm_mhz() or pk["probe_sm_mhz"])
     lfsr_gbs = out_bytes / (ms2 * 1e-3) / 1e9
     print(json.dumps({
         "crc8": {"messages": n, "bytes_each": ln, "ms": ms, "gb_s": gbs,
@@ -86,8 +88,11 @@ def main():
                              "kernel": "lfsr_kernel<64>", "gbit_s": ni * nb / (ms3 * 1e-3) / 1e9,
                              "roofline": {"bound": "alu",
                                           "achieved_tops": ops / (ms3 * 1e-3) / 1e12,
-                                          "peak_tops": lop3_peak_tops(),
-                                          "frac": ops / (ms3 * 1e-3) / 1e12 / lop3_peak_tops()}},
+                                          "peak_tops": peak,
+                                          "frac": ops / (ms3 * 1e-3) / 1e12 / peak,
+                                          "peak_basis": "%d SMs x %.2f LOP3/SM/clk "
+                                                        "(mickey_probe_lop3) x max SM clock"
+                                                        % (pk["n_sm"], pk["lop3_per_sm_clk"])}},
     }), flush=True)
 
 

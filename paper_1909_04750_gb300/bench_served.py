@@ -29,6 +29,7 @@ import torch
 
 from . import workloads
 from .build import build
+from .clocks import ClockSampler
 from .serve import Server
 
 
@@ -59,6 +60,55 @@ def sequential_bound(reqs, ns_per_clock: float, saturate: bool):
     return fin
 
 
+def measure(duration: float = 30.0, rate: float = 1e4, saturate: bool = False,
+            quantum: int = 1 << 15, split_quantum: int = 1 << 17, split_min_bits: int = 0,
+            max_split_groups=None, plain_gbit_s=None, verify=None) -> dict:
+    """Serve the trace; `verify(server, requests, keyset)` checks the served
+    streams after the run and returns a dict for the line."""
+    reqs, keyset = workloads.served_trace(seed=4, rate_per_s=rate, duration_s=duration)
+    bits = np.array([8 * r.n_bytes for r in reqs], np.int64)
+    srv = Server(max(keyset.n, 1), budget_bytes=16 << 30, quantum=quantum,
+                 split_quantum=split_quantum, split_min_bits=split_min_bits,
+                 max_split_groups=max_split_groups)
+    t_clk = lone_serve_ns_per_clock()
+    sampler = ClockSampler(torch.cuda.current_device()).start()
+    srv.run(reqs, realtime=not saturate)
+    clocks = sampler.stop()
+    st = dict(srv.stats)
+    fin = sequential_bound(reqs, t_clk, saturate)
+    lat = fin - (0.0 if saturate else np.array([r.arrival_s for r in reqs]))
+    line = {
+        "metric": "served keystream: p50/p99 latency and aggregate Gbit/s",
+        "mode": "saturation (all requests at t=0)" if saturate else "Poisson arrivals",
+        "requests": len(reqs), "streams": keyset.n,
+        "continue_fraction": float(1 - keyset.n / max(len(reqs), 1)),
+        "offered_gbit_s": float(bits.sum()) / duration / 1e9,
+        "longest_request_bits": int(bits.max()),
+        **st,
+        "config": {"workload": "served: Poisson 10^4 requests/s for %g s, seed 4, 70 %% "
+                               "continuing a resident stream, 1 KiB - 64 MiB per request, "
+                               "16 GiB budget" % duration,
+                   "quantum": quantum, "split_quantum": split_quantum,
+                   "split_min_bits": split_min_bits,
+                   "max_split_groups": srv.max_split_groups, "budget_bytes": 16 << 30},
+        "clocks": clocks,
+    }
+    line["bound"] = {"ns_per_clock": t_clk, "end_ms": float(fin.max()) * 1e3,
+                     "gbit_s": float(bits.sum()) / float(fin.max()) / 1e9,
+                     "p50_ms": float(np.percentile(lat, 50)) * 1e3,
+                     "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+                     "what": "sequential bound: each request starts at its arrival or when "
+                             "its stream's previous request ends, at the split kernel's "
+                             "time per clock alone, unlimited capacity"}
+    if plain_gbit_s:
+        line["busy_vs_plain"] = st["busy_gbit_s"] / plain_gbit_s
+    if verify is not None:
+        line["verified"] = verify(srv, reqs, keyset)
+    srv.free()
+    torch.cuda.empty_cache()
+    return line
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--duration", type=float, default=30.0)
@@ -70,34 +120,8 @@ def main():
     p.add_argument("--max-split-groups", type=int, default=None)
     a = p.parse_args()
     build()
-    reqs, keyset = workloads.served_trace(seed=4, rate_per_s=a.rate, duration_s=a.duration)
-    bits = np.array([8 * r.n_bytes for r in reqs], np.int64)
-    srv = Server(max(keyset.n, 1), budget_bytes=16 << 30, quantum=a.quantum,
-                 split_quantum=a.split_quantum, split_min_bits=a.split_min_bits,
-                 max_split_groups=a.max_split_groups)
-    t_clk = lone_serve_ns_per_clock()
-    srv.run(reqs, realtime=not a.saturate)
-    st = dict(srv.stats)
-    fin = sequential_bound(reqs, t_clk, a.saturate)
-    lat = fin - (0.0 if a.saturate else np.array([r.arrival_s for r in reqs]))
-    line = {
-        "metric": "served keystream: p50/p99 latency and aggregate Gbit/s",
-        "mode": "saturation (all requests at t=0)" if a.saturate else "Poisson arrivals",
-        "requests": len(reqs), "streams": keyset.n,
-        "continue_fraction": float(1 - keyset.n / max(len(reqs), 1)),
-        "offered_gbit_s": float(bits.sum()) / a.duration / 1e9,
-        "longest_request_bits": int(bits.max()),
-        **st,
-        "config": {"quantum": a.quantum, "split_quantum": a.split_quantum,
-                   "split_min_bits": a.split_min_bits,
-                   "max_split_groups": srv.max_split_groups, "budget_bytes": 16 << 30},
-    }
-    line["bound"] = {"ns_per_clock": t_clk, "end_ms": float(fin.max()) * 1e3,
-                     "gbit_s": float(bits.sum()) / float(fin.max()) / 1e9,
-                     "p50_ms": float(np.percentile(lat, 50)) * 1e3,
-                     "p99_ms": float(np.percentile(lat, 99)) * 1e3}
-    print(json.dumps(line), flush=True)
-    srv.free()
+    print(json.dumps(measure(a.duration, a.rate, a.saturate, a.quantum, a.split_quantum,
+                             a.split_min_bits, a.max_split_groups)), flush=True)
 
 
 if __name__ == "__main__":
