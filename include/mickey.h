@@ -322,10 +322,13 @@ MICKEY_API void mickey_server_free(mickey_server *s);
  *              bit l = instance 32g + l.
  *  cuda_stream the work is enqueued there; the call returns at once.
  *  Returns MICKEY_OK, MICKEY_E_ARG (NULL pointer, n == 0, n above the
- *  maximum), MICKEY_E_IVLEN, MICKEY_E_CUDA; it does not set
- *  mickey_last_error.
+ *  maximum), MICKEY_E_IVLEN, MICKEY_E_CUDA, and sets mickey_last_error()
+ *  like the other calls.
  *  The first call on a device looks up the array's device address
  *  (cudaGetSymbolAddress), so make that call before any stream capture.
+ *  After cudaDeviceReset the device has a new context and the array may
+ *  have moved: the next call notices the new context and looks the address
+ *  up again, so it too must come before any stream capture.
  *  Every call uses the same array and leaves its contents behind: calls
  *  whose work overlaps on the GPU race and must be serialised.
  * ------------------------------------------------------------------------ */
