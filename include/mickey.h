@@ -130,6 +130,43 @@ MICKEY_API int mickey_generate(mickey_streams *s, uint64_t n_bits, void *out, in
  * layout cannot hold n_bits. */
 MICKEY_API size_t mickey_output_bytes(size_t n, uint64_t n_bits, int layout);
 
+/* --------------------------------------------------------------------------
+ * Ragged keystream (Sec. IV-D's one-instance-per-lane design with uneven
+ * lengths): stream i continues by its own n_bits[i] bits (0 allowed, at most
+ * 2^34 per call), in one launch.  Each 32-lane group is clocked as often as
+ * its longest lane; every stream's state and position afterwards are those
+ * after exactly its own n_bits[i] bits, so a later call (ragged or
+ * mickey_generate) continues each stream exactly.
+ *
+ *  n_bits       host array of n values (n = mickey_num_streams); copied.
+ *  out          caller-owned DEVICE buffer; nothing is written outside the
+ *               rows and arrays described below.
+ *  out_offsets  host array of byte offsets into out (copied), or NULL for
+ *               the packed arrangement: rows (or group arrays) back to back
+ *               in stream (group) order, mickey_ragged_output_bytes bytes.
+ *  layout       MICKEY_LAYOUT_BYTES: stream i's ceil(n_bits[i] / 8) bytes at
+ *                 out + out_offsets[i], as one row of the bytes layout (any
+ *                 alignment);
+ *               MICKEY_LAYOUT_U32: stream i's n_bits[i] / 32 words at
+ *                 out + out_offsets[i] (4-byte aligned; n_bits[i] % 32 == 0);
+ *               MICKEY_LAYOUT_BITSLICED_U32: out_offsets has ceil(n / 32)
+ *                 entries; group g's C_g words at out + out_offsets[g]
+ *                 (4-byte aligned; 16 for vector stores), C_g the longest
+ *                 n_bits of its lanes; bit l of word t is z_t of instance
+ *                 32g + l while t < n_bits[32g + l], else 0.
+ * Asynchronous on the handle's stream.  Errors (nothing is launched and no
+ * position moves): MICKEY_E_ARG (NULL pointer, a length above 2^34, a
+ * misaligned 32-bit output), MICKEY_E_LAYOUT (MICKEY_LAYOUT_U32_F32, or a
+ * u32 length not a multiple of 32), MICKEY_E_LIMIT (a stream would pass 2^40
+ * bits), MICKEY_E_OOM / MICKEY_E_CUDA.
+ * ------------------------------------------------------------------------ */
+MICKEY_API int mickey_generate_ragged(mickey_streams *s, const uint64_t *n_bits, void *out,
+                                      const uint64_t *out_offsets, int layout);
+
+/* Size in bytes of the packed output of mickey_generate_ragged for these n
+ * lengths; 0 for a layout it does not take. */
+MICKEY_API size_t mickey_ragged_output_bytes(size_t n, const uint64_t *n_bits, int layout);
+
 /* As mickey_generate into a HOST buffer (pinned memory gives full copy
  * speed).  Generation runs in chunks on the device and each chunk is copied
  * back while the next one is generated.  Returns after the data is in

@@ -46,6 +46,8 @@ SIGNATURES = {
     "mickey_set_stream": (c_int, [c_void_p, c_void_p]),
     "mickey_generate": (c_int, [c_void_p, c_uint64, c_void_p, c_int]),
     "mickey_output_bytes": (c_size_t, [c_size_t, c_uint64, c_int]),
+    "mickey_generate_ragged": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
+    "mickey_ragged_output_bytes": (c_size_t, [c_size_t, c_void_p, c_int]),
     "mickey_generate_host": (c_int, [c_void_p, c_uint64, c_void_p, c_int]),
     "mickey_sync": (c_int, [c_void_p]),
     "mickey_num_streams": (c_size_t, [c_void_p]),

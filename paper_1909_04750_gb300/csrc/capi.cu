@@ -44,6 +44,11 @@ struct mickey_streams {
   size_t stage_bytes = 0;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+  // mickey_generate_ragged: device copies of the per-stream lengths and
+  // output offsets, and the event after the last launch that reads them
+  uint64_t *d_ragged = nullptr;
+  size_t ragged_words = 0;
+  cudaEvent_t ev_ragged = nullptr;
 };
 
 namespace {
@@ -128,6 +133,8 @@ void release(mickey_streams *s) {
   cudaFree(s->d_inputs);
   cudaFree(s->d_err);
   cudaFree(s->d_flags);
+  cudaFree(s->d_ragged);
+  if (s->ev_ragged) cudaEventDestroy(s->ev_ragged);
   delete s;
 }
 
@@ -284,6 +291,26 @@ int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
   return MICKEY_OK;
 }
 
+// Byte offsets of the packed ragged output (rows, or for the bitsliced layout
+// the groups' word arrays, back to back) into offs; returns the total size.
+uint64_t ragged_packed(size_t n, const uint64_t *n_bits, int layout, uint64_t *offs) {
+  uint64_t off = 0;
+  if (layout == MICKEY_LAYOUT_BITSLICED_U32) {
+    for (size_t g = 0; g * 32 < n; ++g) {
+      uint64_t c = 0;
+      for (size_t i = 32 * g; i < n && i < 32 * g + 32; ++i) c = std::max(c, n_bits[i]);
+      if (offs) offs[g] = off;
+      off += 4 * c;
+    }
+    return off;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    if (offs) offs[i] = off;
+    off += layout == MICKEY_LAYOUT_U32 ? n_bits[i] / 8 : (n_bits[i] + 7) / 8;
+  }
+  return off;
+}
+
 }  // namespace
 
 namespace mickey {
@@ -365,6 +392,80 @@ int mickey_generate(mickey_streams *s, uint64_t n_bits, void *out, int layout) {
 
 size_t mickey_output_bytes(size_t n, uint64_t n_bits, int layout) {
   return out_bytes(n, n_bits, layout);
+}
+
+int mickey_generate_ragged(mickey_streams *s, const uint64_t *n_bits, void *out,
+                           const uint64_t *out_offsets, int layout) {
+  if (!s || !n_bits || !out) return fail(MICKEY_E_ARG, "handle, n_bits and out must not be NULL");
+  if (layout != MICKEY_LAYOUT_BITSLICED_U32 && layout != MICKEY_LAYOUT_BYTES &&
+      layout != MICKEY_LAYOUT_U32)
+    return fail(MICKEY_E_LAYOUT, "ragged generation takes the bitsliced, bytes or u32 layout "
+                "(got %d)", layout);
+  const size_t n = s->n, G = s->G;
+  const size_t n_off = layout == MICKEY_LAYOUT_BITSLICED_U32 ? G : n;
+  uint64_t any = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (n_bits[i] > kMaxBitsPerCall)
+      return fail(MICKEY_E_ARG, "n_bits[%zu] = %llu is above 2^34 per call", i,
+                  (unsigned long long)n_bits[i]);
+    if (s->pos[i] + n_bits[i] > MICKEY_MAX_STREAM_BITS)
+      return fail(MICKEY_E_LIMIT, "stream %zu would pass 2^40 keystream bits", i);
+    if (layout == MICKEY_LAYOUT_U32 && n_bits[i] % 32)
+      return fail(MICKEY_E_LAYOUT, "the u32 layout needs n_bits[%zu] %% 32 == 0", i);
+    any |= n_bits[i];
+  }
+  std::vector<uint64_t> h(n + n_off);
+  std::copy(n_bits, n_bits + n, h.begin());
+  uint64_t *offs = h.data() + n;
+  if (out_offsets)
+    std::copy(out_offsets, out_offsets + n_off, offs);
+  else
+    ragged_packed(n, n_bits, layout, offs);
+  const uintptr_t base = reinterpret_cast<uintptr_t>(out);
+  if (layout != MICKEY_LAYOUT_BYTES) {
+    for (size_t k = 0; k < n_off; ++k) {
+      uint64_t c = layout == MICKEY_LAYOUT_U32 ? n_bits[k] : 0;
+      if (layout == MICKEY_LAYOUT_BITSLICED_U32)
+        for (size_t i = 32 * k; i < n && i < 32 * k + 32; ++i) c = std::max(c, n_bits[i]);
+      if (c && (base + offs[k]) % 4)
+        return fail(MICKEY_E_ARG, "output %zu of a 32-bit layout is not 4-byte aligned", k);
+    }
+  }
+  if (!any) return ok();                              // nothing to generate
+  const size_t words = n + n_off;
+  if (s->ragged_words < words) {
+    if (s->d_ragged) {
+      CUDA_TRY(cudaStreamSynchronize(s->stream), "sync");
+      cudaFree(s->d_ragged);
+      s->d_ragged = nullptr;
+      s->ragged_words = 0;
+    }
+    CUDA_TRY(cudaMalloc(&s->d_ragged, words * 8), "cudaMalloc(ragged lengths)");
+    s->ragged_words = words;
+  }
+  if (!s->ev_ragged)
+    CUDA_TRY(cudaEventCreateWithFlags(&s->ev_ragged, cudaEventDisableTiming), "event");
+  // the previous ragged launch (perhaps on another stream) has read its copy
+  CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_ragged, 0), "wait");
+  CUDA_TRY(cudaMemcpyAsync(s->d_ragged, h.data(), words * 8, cudaMemcpyHostToDevice, s->stream),
+           "H2D ragged lengths");
+  RaggedArgs ra{s->d_state, s->G, s->Gpad, n, s->d_ragged, s->d_ragged + n,
+                static_cast<uint8_t *>(out)};
+  CUDA_TRY(launch_ragged(ra, layout, s->stream), "ragged_kernel launch");
+  CUDA_TRY(cudaEventRecord(s->ev_ragged, s->stream), "record");
+  for (size_t i = 0; i < n; ++i) s->pos[i] += n_bits[i];
+  return ok();
+}
+
+size_t mickey_ragged_output_bytes(size_t n, const uint64_t *n_bits, int layout) {
+  if (!n_bits) return 0;
+  if (layout != MICKEY_LAYOUT_BITSLICED_U32 && layout != MICKEY_LAYOUT_BYTES &&
+      layout != MICKEY_LAYOUT_U32)
+    return 0;
+  if (layout == MICKEY_LAYOUT_U32)
+    for (size_t i = 0; i < n; ++i)
+      if (n_bits[i] % 32) return 0;
+  return size_t(ragged_packed(n, n_bits, layout, nullptr));
 }
 
 int mickey_generate_host(mickey_streams *s, uint64_t n_bits, void *host_out, int layout) {

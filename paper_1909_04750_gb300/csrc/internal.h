@@ -90,6 +90,19 @@ struct PersistArgs {
   int *err;
 };
 
+// Ragged generation on a handle (ragged.cu): stream i continues by
+// n_bits[i] bits; its output starts at byte offsets[i] of out (row layouts)
+// or, for the bitsliced layout, group g's words start at offsets[g].
+struct RaggedArgs {
+  uint32_t *state;          // kStateRows * Gpad words, read and written back
+  uint32_t G, Gpad;
+  uint64_t n;
+  const uint64_t *n_bits;   // n values, device
+  const uint64_t *offsets;  // n (row layouts) or G (bitsliced) byte offsets, device
+  uint8_t *out;
+};
+cudaError_t launch_ragged(const RaggedArgs &a, int layout, cudaStream_t st);
+
 // p == nullptr: grid mode (one thread per group); else persistent mode.
 // stage: row layouts stage four tiles per row and write 16-byte chunks
 // (used when n_bits % 128 == 0 and `out` is 16-byte aligned).

@@ -22,6 +22,10 @@ instances x ``n_bits``, ``--reps`` times.
 ``crc8``: CRC-8 (0x1D, preset and final XOR 0xFF) of n messages of
 ``n_bits / 8`` bytes each (random, device-resident), ``--reps`` times.
 
+``ragged``: a handle of n instances (seed 2) continues every stream by its
+own length in one mickey_generate_ragged call, ``--reps`` times: every
+length ``n_bits`` (``--spread 0``) or uniform in [n_bits - spread, n_bits].
+
 ``serve``: a server holding n streams serves one request of ``n_bits`` bits
 per stream ``--reps`` times, each in one step of split groups only (the
 split kernel launches one warp per group, so its counters come from the
@@ -42,8 +46,9 @@ def main():
     p.add_argument("--n-bits", type=int, default=2048)
     p.add_argument("--layout", default="bytes")
     p.add_argument("--reps", type=int, default=2)
-    p.add_argument("--case", choices=("plain", "split", "serve", "crc8", "batched", "lfsr"),
-                   default="plain")
+    p.add_argument("--case", choices=("plain", "split", "serve", "crc8", "batched", "lfsr",
+                                      "ragged"), default="plain")
+    p.add_argument("--spread", type=int, default=0)
     p.add_argument("--autotune", action="store_true")
     a = p.parse_args()
     build()
@@ -89,6 +94,20 @@ def main():
             srv.run(reqs, realtime=False)
         torch.cuda.synchronize()
         srv.free()
+        print("ok", vars(a))
+        return
+    if a.case == "ragged":
+        import numpy as np
+        s = workloads.plain_scale(a.n)
+        st = Streams(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
+        rng = np.random.default_rng(1)
+        nb = np.full(a.n, a.n_bits, np.uint64)
+        if a.spread:
+            nb = rng.integers(a.n_bits - a.spread, a.n_bits + 1, a.n).astype(np.uint64)
+        out = None
+        for _ in range(a.reps):
+            out, _ = st.generate_ragged(nb, a.layout, out=out)
+        st.sync()
         print("ok", vars(a))
         return
     if a.case == "split":

@@ -87,6 +87,35 @@ class Streams:
         N.check(self._L.mickey_generate(self._h, n_bits, ctypes.c_void_p(out.data_ptr()), lay))
         return out
 
+    def generate_ragged(self, n_bits, layout="bytes", out: torch.Tensor | None = None,
+                        offsets=None):
+        """Stream i continues by n_bits[i] bits in one launch.  Returns the
+        output tensor (packed, allocated here when `out` is None) and the
+        byte offsets used (per stream, or per group for "bitsliced")."""
+        lay = layout_id(layout)
+        nb = np.ascontiguousarray(n_bits, np.uint64)
+        if nb.shape != (self.n,):
+            raise N.MickeyError(N.E_ARG, "n_bits needs one value per stream")
+        if offsets is None:
+            total = int(self._L.mickey_ragged_output_bytes(self.n, nb.ctypes.data, lay))
+            if total == 0 and nb.any():
+                raise N.MickeyError(N.E_LAYOUT, "layout cannot hold these lengths")
+            if out is None:
+                out = torch.empty(max(total, 16), dtype=torch.uint8, device="cuda")
+            elif out.numel() * out.element_size() < total:
+                raise N.MickeyError(N.E_ARG, "output tensor too small")
+            offs = None
+        else:
+            offs = np.ascontiguousarray(offsets, np.uint64)
+        self._L.mickey_set_stream(self._h, _stream_ptr(self.stream))
+        N.check(self._L.mickey_generate_ragged(self._h, nb.ctypes.data,
+                                               ctypes.c_void_p(out.data_ptr()),
+                                               offs.ctypes.data if offs is not None else None,
+                                               lay))
+        if offs is None:
+            offs = packed_offsets(nb, lay)
+        return out, offs
+
     def generate_host(self, n_bits: int, layout="bytes", out: torch.Tensor | None = None):
         """Next n_bits into a host tensor (pinned if allocated here)."""
         lay = layout_id(layout)
@@ -142,6 +171,21 @@ class Streams:
             self.free()
         except Exception:
             pass
+
+
+def packed_offsets(n_bits, layout) -> np.ndarray:
+    """Byte offsets of the packed output of a ragged call: per stream for the
+    row layouts, per 32-lane group for the bitsliced layout."""
+    nb = np.asarray(n_bits, np.uint64).astype(np.int64)
+    lay = layout_id(layout)
+    if lay == N.LAYOUT_BITSLICED_U32:
+        pad = np.zeros(-nb.size % 32, np.int64)
+        sizes = 4 * np.concatenate([nb, pad]).reshape(-1, 32).max(axis=1)
+    elif lay == N.LAYOUT_U32:
+        sizes = nb // 8
+    else:
+        sizes = (nb + 7) // 8
+    return np.concatenate(([0], np.cumsum(sizes)[:-1])).astype(np.uint64)
 
 
 def tables() -> np.ndarray:

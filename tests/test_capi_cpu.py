@@ -176,3 +176,35 @@ def test_plain_c_program_compiles_and_links(L, tmp_path):
                     "-L", os.path.dirname(B.LIB), "-lmickey",
                     "-Wl,-rpath," + os.path.dirname(B.LIB)], check=True)
     assert os.path.exists(exe)
+
+
+def test_ragged_host_side_errors_and_sizes(L):
+    nb = np.array([0, 1, 7, 33, 8191] + [64] * 30, np.uint64)
+    # no handle: rejected before any device work
+    assert L.mickey_generate_ragged(None, nb.ctypes.data, ctypes.c_void_p(16), None,
+                                    N.LAYOUT_BYTES) == N.E_ARG
+    assert L.mickey_last_error() == N.E_ARG
+    # packed sizes: rows back to back, or the groups' word arrays
+    assert L.mickey_ragged_output_bytes(nb.size, nb.ctypes.data, N.LAYOUT_BYTES) == \
+        int(((nb + 7) // 8).sum())
+    assert L.mickey_ragged_output_bytes(nb.size, nb.ctypes.data, N.LAYOUT_BITSLICED_U32) == \
+        4 * (8191 + 64)
+    assert L.mickey_ragged_output_bytes(nb.size, nb.ctypes.data, N.LAYOUT_U32) == 0
+    w = np.array([32, 0, 64], np.uint64)
+    assert L.mickey_ragged_output_bytes(3, w.ctypes.data, N.LAYOUT_U32) == 12
+    assert L.mickey_ragged_output_bytes(3, w.ctypes.data, N.LAYOUT_U32_F32) == 0
+    assert L.mickey_ragged_output_bytes(3, None, N.LAYOUT_BYTES) == 0
+
+
+def test_packed_offsets_match_library_sizes(L):
+    from paper_1909_04750_gb300.streams import packed_offsets
+    rng = np.random.default_rng(4)
+    nb = rng.integers(0, 5000, 77).astype(np.uint64)
+    for lay in (N.LAYOUT_BYTES, N.LAYOUT_BITSLICED_U32):
+        offs = packed_offsets(nb, lay)
+        total = L.mickey_ragged_output_bytes(nb.size, nb.ctypes.data, lay)
+        if lay == N.LAYOUT_BYTES:
+            assert offs[-1] + (nb[-1] + 7) // 8 == total
+        else:
+            last = 4 * int(nb[64:].max())
+            assert int(offs[-1]) + last == total
