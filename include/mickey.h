@@ -291,6 +291,19 @@ MICKEY_API int mickey_batch_run(mickey_batch *b, const void *keys, const void *i
  * the split path.  Re-captures the graph. */
 MICKEY_API int mickey_batch_set_config(mickey_batch *b, int unroll, int blocks_per_sm,
                                        uint64_t split_clocks);
+/* Where the split groups run (re-captures the graph):
+ *   MICKEY_BATCH_SPLIT_SHARED (default): in the persistent kernel's warps,
+ *     before its thread items; a long split warp keeps its SM sub-partition
+ *     to itself (the shortest critical path for one batch);
+ *   MICKEY_BATCH_SPLIT_OWN: in a kernel of one-warp blocks beside the thread
+ *     kernel (parallel graph branches), so blocks of short thread items
+ *     retire and free their registers while the split warps run on (batches
+ *     back to back on several CUDA streams).
+ * mickey_batch_get_split_mode returns the mode (or MICKEY_E_ARG). */
+#define MICKEY_BATCH_SPLIT_SHARED 0
+#define MICKEY_BATCH_SPLIT_OWN 1
+MICKEY_API int mickey_batch_set_split_mode(mickey_batch *b, int mode);
+MICKEY_API int mickey_batch_get_split_mode(const mickey_batch *b);
 /* split_clocks / split_groups may be NULL. */
 MICKEY_API int mickey_batch_get_config(const mickey_batch *b, int *unroll, int *blocks_per_sm,
                                        uint64_t *split_clocks, uint32_t *split_groups);

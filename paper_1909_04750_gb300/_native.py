@@ -18,6 +18,7 @@ E_ARG, E_IVLEN, E_LIMIT, E_LAYOUT, E_OOM, E_CUDA, E_TIMEOUT, E_STATE = range(-1,
 LAYOUT_BITSLICED_U32, LAYOUT_BYTES, LAYOUT_U32, LAYOUT_U32_F32 = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE = 0, 1
 MODE_AUTO, MODE_GRID, MODE_PERSISTENT, MODE_PERSISTENT2 = 0, 1, 2, 3
+BATCH_SPLIT_SHARED, BATCH_SPLIT_OWN = 0, 1
 
 
 class TuneResult(ctypes.Structure):
@@ -73,6 +74,8 @@ SIGNATURES = {
     "mickey_batch_run": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int]),
     "mickey_batch_set_config": (c_int, [c_void_p, c_int, c_int, c_uint64]),
     "mickey_batch_get_config": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "mickey_batch_set_split_mode": (c_int, [c_void_p, c_int]),
+    "mickey_batch_get_split_mode": (c_int, [c_void_p]),
     "mickey_batch_sync": (c_int, [c_void_p]),
     "mickey_batch_free": (None, [c_void_p]),
     "mickey_server_create": (c_void_p, [c_size_t, ctypes.c_uint32, c_void_p]),

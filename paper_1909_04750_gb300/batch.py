@@ -52,8 +52,11 @@ class Batch:
     def sync(self):
         N.check(self._L.mickey_batch_sync(self._h))
 
-    def set_config(self, unroll: int, blocks_per_sm: int, split_clocks: int = 0):
+    def set_config(self, unroll: int, blocks_per_sm: int, split_clocks: int = 0,
+                   split_mode: int | None = None):
         N.check(self._L.mickey_batch_set_config(self._h, unroll, blocks_per_sm, split_clocks))
+        if split_mode is not None and split_mode != self._L.mickey_batch_get_split_mode(self._h):
+            N.check(self._L.mickey_batch_set_split_mode(self._h, split_mode))
 
     def get_config(self):
         u, b = ctypes.c_int(), ctypes.c_int()
@@ -61,7 +64,8 @@ class Batch:
         N.check(self._L.mickey_batch_get_config(self._h, ctypes.byref(u), ctypes.byref(b),
                                                 ctypes.byref(sc), ctypes.byref(sg)))
         return {"unroll": int(u.value), "blocks_per_sm": int(b.value),
-                "split_clocks": int(sc.value), "split_groups": int(sg.value)}
+                "split_clocks": int(sc.value), "split_groups": int(sg.value),
+                "split_mode": int(self._L.mickey_batch_get_split_mode(self._h))}
 
     def rows(self, out: torch.Tensor):
         """Per-stream byte strings (host), for checking."""
@@ -105,12 +109,13 @@ def tune(batch: Batch, keys, ivs, out: torch.Tensor, refresh: bool = False) -> d
     with _lock:
         hit = None if refresh else _load().get(key)
     if hit is not None:
-        batch.set_config(hit["unroll"], hit["blocks_per_sm"], hit["split_clocks"])
+        batch.set_config(hit["unroll"], hit["blocks_per_sm"], hit["split_clocks"],
+                         hit.get("split_mode", N.BATCH_SPLIT_SHARED))
         return hit
     cands = []
 
-    def trial(u, b, sc):
-        batch.set_config(u, b, sc)
+    def trial(u, b, sc, mode=N.BATCH_SPLIT_SHARED):
+        batch.set_config(u, b, sc, mode)
         c = dict(batch.get_config(), ms=_time(batch, keys, ivs, out))
         cands.append(c)
         return c
@@ -127,7 +132,11 @@ def tune(batch: Batch, keys, ivs, out: torch.Tensor, refresh: bool = False) -> d
     best = min(cands, key=lambda c: c["ms"])
     trial(2, best["blocks_per_sm"], best["split_clocks"])
     best = min(cands, key=lambda c: c["ms"])
-    batch.set_config(best["unroll"], best["blocks_per_sm"], best["split_clocks"])
+    if best["split_groups"]:
+        trial(best["unroll"], best["blocks_per_sm"], best["split_clocks"], N.BATCH_SPLIT_OWN)
+        best = min(cands, key=lambda c: c["ms"])
+    batch.set_config(best["unroll"], best["blocks_per_sm"], best["split_clocks"],
+                     best["split_mode"])
     entry = dict(best, candidates=cands)
     with _lock:
         cache = _load()

@@ -23,6 +23,7 @@ import statistics
 import numpy as np
 import torch
 
+from . import _native as N
 from . import workloads
 from .batch import Batch, tune
 from .build import build
@@ -63,7 +64,7 @@ def lone_group_ns_per_clock(n_bits: int = 1 << 16) -> float:
 
 
 def measure(runs: int = 3, n: int = workloads.BATCHED["n"], steady: int = 12,
-            pipeline: int = 4, steady_split: int = 0, plain_gbit_s=None, verify=None) -> dict:
+            pipeline: int = 0, steady_split: int = 0, plain_gbit_s=None, verify=None) -> dict:
     """Time one replay of the batched workload `runs` times (and, with
     `steady`, batches back to back); `verify(streamset, batch, out)` checks
     the last replay's output and returns a dict for the line."""
@@ -109,21 +110,24 @@ def measure(runs: int = 3, n: int = workloads.BATCHED["n"], steady: int = 12,
         line["vs_plain"] = line["value"] / plain_gbit_s
     if verify is not None:
         line["verified"] = verify(s, b, out)
+    max_clocks = b.max_clocks
+    b.free()
+    del out
+    torch.cuda.empty_cache()
     if steady:
-        cfg = dict(tuned)
-        if steady_split:
-            cfg["split_clocks"] = b.max_clocks // steady_split
-        b.free()
-        del out
-        torch.cuda.empty_cache()
         sampler = ClockSampler(torch.cuda.current_device()).start()
-        line["steady"] = steady_state(b, s, keys, ivs, cfg, steady, pipeline)
+        if steady_split or pipeline:
+            cfg = dict(tuned)
+            if steady_split:
+                cfg["split_clocks"] = max_clocks // steady_split
+            line["steady"] = steady_state(s, keys, ivs, cfg, steady, pipeline or 4)
+        else:
+            line["steady"] = steady_sweep(s, keys, ivs, tuned, max_clocks)
         line["steady"]["clocks"] = sampler.stop()
-        line["steady"]["split_clocks"] = cfg["split_clocks"]
+        line["steady"]["what"] = ("batches of the same workload back to back, round-robin over "
+                                  "`pipeline` handles on their own CUDA streams")
         if plain_gbit_s:
             line["steady"]["vs_plain"] = line["steady"]["gbit_s"] / plain_gbit_s
-    else:
-        b.free()
     return line
 
 
@@ -134,7 +138,9 @@ def main():
     p.add_argument("--plain-gbit-s", type=float, default=None,
                    help="plain-workload throughput for the work bound")
     p.add_argument("--steady", type=int, default=0, help="batches for the steady-state rate")
-    p.add_argument("--pipeline", type=int, default=4, help="handles (CUDA streams) in flight")
+    p.add_argument("--pipeline", type=int, default=0,
+                   help="handles (CUDA streams) in flight (0: sweep 4 and 8 with the split "
+                        "arrangements)")
     p.add_argument("--steady-split", type=int, default=0,
                    help="split threshold for the steady-state run as max_clocks / this "
                         "(0: the tuned one)")
@@ -144,13 +150,14 @@ def main():
                              a.plain_gbit_s)), flush=True)
 
 
-def steady_state(b0, s, keys, ivs, tuned, k: int, pipeline: int) -> dict:
+def steady_state(s, keys, ivs, cfg, k: int, pipeline: int) -> dict:
     """K batches back to back over `pipeline` handles on their own streams."""
     streams = [torch.cuda.Stream() for _ in range(pipeline)]
     hs = [Batch(s.n_bits, s.iv_lens, stream=st) for st in streams]
     outs = [torch.empty(hs[0].output_bytes, dtype=torch.uint8, device="cuda") for _ in hs]
     for h, o in zip(hs, outs):
-        h.set_config(tuned["unroll"], tuned["blocks_per_sm"], tuned["split_clocks"])
+        h.set_config(cfg["unroll"], cfg["blocks_per_sm"], cfg["split_clocks"],
+                     cfg.get("split_mode", N.BATCH_SPLIT_SHARED))
         h.run(keys, ivs, o)                              # capture + warm-up
     torch.cuda.synchronize()
     start = torch.cuda.Event(enable_timing=True)
@@ -168,9 +175,29 @@ def steady_state(b0, s, keys, ivs, tuned, k: int, pipeline: int) -> dict:
     ms = max(start.elapsed_time(e) for e in done)
     for h in hs:
         h.free()
+    del outs
+    torch.cuda.empty_cache()
     bits = int(s.n_bits.sum()) * k
     return {"batches": k, "pipeline": pipeline, "ms": ms, "ms_per_batch": ms / k,
-            "gbit_s": bits / (ms * 1e-3) / 1e9}
+            "gbit_s": bits / (ms * 1e-3) / 1e9, "split_clocks": cfg["split_clocks"],
+            "split_mode": ["shared", "own"][cfg.get("split_mode", N.BATCH_SPLIT_SHARED)],
+            "blocks_per_sm": cfg["blocks_per_sm"], "unroll": cfg["unroll"]}
+
+
+def steady_sweep(s, keys, ivs, tuned, max_clocks: int, rounds: int = 3) -> dict:
+    """The steady-state rate over a few launch arrangements (split mode,
+    split threshold, batches in flight); returns the best with every
+    candidate."""
+    cands = []
+    for mode in (N.BATCH_SPLIT_SHARED, N.BATCH_SPLIT_OWN):
+        for sc in sorted({tuned["split_clocks"], max_clocks // 16}):
+            for pipe in (4, 8):
+                cfg = dict(tuned, split_clocks=sc, split_mode=mode)
+                cands.append(steady_state(s, keys, ivs, cfg, rounds * pipe, pipe))
+    best = dict(max(cands, key=lambda c: c["gbit_s"]))
+    best["candidates"] = [{k: c[k] for k in ("gbit_s", "split_mode", "split_clocks", "pipeline")}
+                          for c in cands]
+    return best
 
 
 if __name__ == "__main__":

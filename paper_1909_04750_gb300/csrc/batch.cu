@@ -9,13 +9,21 @@
 // offset (in the caller's stream order).
 //
 // Run (device, captured once as a CUDA graph and replayed): key/IV loading
-// through the sorting permutation, preclock, then one persistent keystream
-// kernel whose warps take work items from an atomic counter.  The first
-// n_split items are the longest groups, one per warp (split path: the warp
-// clocks one group, several times less time per clock, for the groups that
-// bound the run); the rest are 32 consecutive groups, one per thread.  Items
-// are numbered longest first, so the longest groups start first
-// (longest-processing-time order) and the short ones fill in behind them.
+// through the sorting permutation, preclock, then the keystream.  The first
+// n_split groups, the longest, run one per warp (split path: the warp clocks
+// one group, several times less time per clock, for the groups that bound
+// the run); the rest 32 consecutive groups per warp item, one per thread.
+// Items are taken from atomic counters longest first (longest processing
+// time first).  Two arrangements (the split mode):
+//   shared  one persistent kernel: its warps take the split items first,
+//           then the thread items.  A long split warp keeps its SM
+//           sub-partition to itself, which is best for one batch's critical
+//           path.
+//   own     the split groups in a kernel of one-warp blocks (one per SM
+//           sub-partition) beside the thread kernel, as parallel branches of
+//           the graph.  A block of short thread items then retires, and frees
+//           its registers for the next batch's work, however long the split
+//           warps run: the arrangement for batches back to back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,8 +54,9 @@ struct BatchArgs {
   const uint64_t *slot_bits; // 32*Gpad: keystream bits of the slot's stream (0: padding)
   const uint64_t *group_bits;// Gpad: clocks of the group (its longest lane)
   uint32_t n_split;          // groups 0..n_split-1 run on a whole warp each
-  uint32_t n_items;          // n_split + ceil((G - n_split) / 32)
-  uint32_t *queue;           // item counter, zero at launch
+  uint32_t split_items;      // split items this kernel takes (n_split, or 0 in "own" mode)
+  uint32_t n_items;          // split_items + ceil((G - n_split) / 32)
+  uint32_t *queue;           // [0]: split-group counter, [1]: item counter, zero at launch
   const BatchParams *params;
 };
 
@@ -202,9 +211,27 @@ __device__ __noinline__ void split_group(const uint32_t *state, size_t P, uint32
   __syncwarp();
 }
 
-// Work items in queue order: first one item per split group (groups
-// 0 .. n_split-1, the longest), each run by a whole warp; then items of 32
-// consecutive groups, one per thread.
+// Split kernel: one-warp blocks take the split groups (0 .. n_split-1,
+// longest first) one at a time.
+__global__ void __launch_bounds__(32) batch_split_kernel(BatchArgs a) {
+  __shared__ uint32_t zs[64];
+  const uint32_t lane = threadIdx.x;
+  uint8_t *out = a.params->out;
+#pragma unroll 1
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(a.queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= a.n_split) break;
+    const uint64_t slot = uint64_t(item) * 32 + lane;
+    split_group(a.state, a.Gpad, item, a.group_bits[item], out + a.slot_off[slot],
+                a.slot_bits[slot], lane, zs, zs + 32);
+  }
+}
+
+// Persistent kernel: its first split_items items are split groups, run by
+// a whole warp each; then items of 32 consecutive groups from group n_split
+// on, one group per thread.
 template <int U>
 __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
   __shared__ uint32_t zs[2 * 32 * kBatchThreads];
@@ -213,10 +240,10 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
 #pragma unroll 1
   for (;;) {
     uint32_t item = 0;
-    if (lane == 0) item = atomicAdd(a.queue, 1u);
+    if (lane == 0) item = atomicAdd(a.queue + 1, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
-    if (item < a.n_split) {
+    if (item < a.split_items) {
       // the warp's own 32 columns of rows 0 and 1 of the tile buffer
       const uint64_t slot = uint64_t(item) * 32 + lane;
       uint32_t *zb = zs + (threadIdx.x & ~31u);
@@ -224,7 +251,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
                   a.slot_bits[slot], lane, zb, zb + kBatchThreads);
       continue;
     }
-    const uint32_t g = a.n_split + (item - a.n_split) * 32 + lane;
+    const uint32_t g = a.n_split + (item - a.split_items) * 32 + lane;
     if (g < a.G)
       batch_group<U>(a, out, g, zs + threadIdx.x, zs + 32 * kBatchThreads + threadIdx.x);
   }
@@ -245,6 +272,7 @@ struct mickey_batch {
   int unroll = 4, blocks_per_sm = 2;
   uint64_t split_clocks = 0;      // groups longer than this use the split path (0: none)
   uint32_t n_split = 0;
+  int split_mode = MICKEY_BATCH_SPLIT_SHARED;
   // device
   uint8_t *d_in = nullptr;        // keys (10n), ivs (10n), iv_lens (4n) in caller order
   uint32_t *d_perm = nullptr;     // 32*Gpad
@@ -274,36 +302,55 @@ void batch_release(mickey_batch *b) {
   delete b;
 }
 
-// Capture load + preclock + persistent keystream into a graph.
+// Capture load + preclock, then the split kernel and the thread kernel as
+// two parallel branches, into a graph.
 cudaError_t capture(mickey_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
-  cudaStream_t cs = nullptr;
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     const size_t n = b->n;
-    cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), cs);
+    cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(uint32_t), cs);
     LoadArgs la{b->d_in, b->d_in + 10 * n, reinterpret_cast<const uint32_t *>(b->d_in + 20 * n),
                 n, b->d_perm, b->G, b->Gpad, b->d_scratch, b->d_err};
     launch_load(la, cs);
     PreclockArgs pa{b->d_scratch, b->d_state, b->G, b->Gpad};
     launch_preclock(pa, cs);
+    const bool own = b->split_mode == MICKEY_BATCH_SPLIT_OWN && b->n_split;
+    const uint32_t split_items = own ? 0u : b->n_split;
     BatchArgs ba{b->d_state, b->G, b->Gpad, b->d_slot, b->d_slot + 32 * size_t(b->Gpad),
-                 b->d_slot + 64 * size_t(b->Gpad), b->n_split,
-                 b->n_split + (b->G - b->n_split + 31) / 32, b->d_queue, b->d_params};
-    const uint32_t grid = uint32_t(b->sm_count * b->blocks_per_sm);
-    if (b->unroll == 2)
-      batch_kernel<2><<<grid, kBatchThreads, 0, cs>>>(ba);
-    else
-      batch_kernel<4><<<grid, kBatchThreads, 0, cs>>>(ba);
+                 b->d_slot + 64 * size_t(b->Gpad), b->n_split, split_items,
+                 split_items + (b->G - b->n_split + 31) / 32, b->d_queue, b->d_params};
+    if (own) {   // the split groups on a branch of their own
+      cudaEventRecord(fork, cs);
+      cudaStreamWaitEvent(cs2, fork, 0);
+      const uint32_t warps = std::min<uint32_t>(b->n_split, uint32_t(b->sm_count) * 4u);
+      batch_split_kernel<<<warps, 32, 0, cs2>>>(ba);
+      cudaEventRecord(join, cs2);
+    }
+    if (ba.n_items) {
+      const uint32_t grid = uint32_t(b->sm_count * b->blocks_per_sm);
+      if (b->unroll == 2)
+        batch_kernel<2><<<grid, kBatchThreads, 0, cs>>>(ba);
+      else
+        batch_kernel<4><<<grid, kBatchThreads, 0, cs>>>(ba);
+    }
+    if (own) cudaStreamWaitEvent(cs, join, 0);
     e = cudaStreamEndCapture(cs, &b->graph);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-  cudaStreamDestroy(cs);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (cs2) cudaStreamDestroy(cs2);
+  if (cs) cudaStreamDestroy(cs);
   return e;
 }
 
@@ -382,7 +429,7 @@ MICKEY_API mickey_batch *mickey_batch_create(const uint32_t *iv_lens, const uint
             cudaMalloc(&b->d_slot, slot.size() * 8) == cudaSuccess &&
             cudaMalloc(&b->d_state, size_t(kStateRows) * b->Gpad * 4) == cudaSuccess &&
             cudaMalloc(&b->d_scratch, size_t(kScratchRows + 1) * b->Gpad * 4) == cudaSuccess &&
-            cudaMalloc(&b->d_queue, 4) == cudaSuccess &&
+            cudaMalloc(&b->d_queue, 8) == cudaSuccess &&
             cudaMalloc(&b->d_err, 4) == cudaSuccess &&
             cudaMalloc(&b->d_params, sizeof(BatchParams)) == cudaSuccess;
   if (ok) {
@@ -449,6 +496,20 @@ MICKEY_API int mickey_batch_set_config(mickey_batch *b, int unroll, int blocks_p
     while (ns < b->G && b->group_clocks[ns] > split_clocks) ++ns;
   b->n_split = ns;
   return capture(b) == cudaSuccess ? MICKEY_OK : MICKEY_E_CUDA;
+}
+
+MICKEY_API int mickey_batch_set_split_mode(mickey_batch *b, int mode) {
+  if (!b || (mode != MICKEY_BATCH_SPLIT_SHARED && mode != MICKEY_BATCH_SPLIT_OWN))
+    return set_error(MICKEY_E_ARG, "split mode must be MICKEY_BATCH_SPLIT_SHARED or _OWN");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(MICKEY_E_CUDA, "sync");
+  b->split_mode = mode;
+  return capture(b) == cudaSuccess ? set_error(MICKEY_OK, "")
+                                   : set_error(MICKEY_E_CUDA, "graph capture failed");
+}
+
+MICKEY_API int mickey_batch_get_split_mode(const mickey_batch *b) {
+  if (!b) return set_error(MICKEY_E_ARG, "NULL handle");
+  return b->split_mode;
 }
 
 MICKEY_API int mickey_batch_get_config(const mickey_batch *b, int *unroll, int *blocks_per_sm,

@@ -73,9 +73,11 @@ def test_batch_graph_replay_and_host_inputs():
     _check(b, o1, s, idx=range(0, 700, 7))
 
 
+@pytest.mark.parametrize("split_mode", [N.BATCH_SPLIT_SHARED, N.BATCH_SPLIT_OWN])
 @pytest.mark.parametrize("split_clocks", [1, 3000, 7000])
-def test_split_path_every_stream(split_clocks):
-    # groups needing more clocks than split_clocks run one per warp
+def test_split_path_every_stream(split_clocks, split_mode):
+    # groups needing more clocks than split_clocks run one per warp, in the
+    # persistent kernel's warps or in a kernel of their own
     from paper_1909_04750_gb300.batch import Batch
     s = workloads.batched(2000)
     rng = np.random.default_rng(7)
@@ -83,9 +85,9 @@ def test_split_path_every_stream(split_clocks):
     nb[:6] = [11999, 11998, 1, 0, 31, 8193]
     s.n_bits = nb
     b = Batch(nb, s.iv_lens)
-    b.set_config(4, 2, split_clocks)
+    b.set_config(4, 2, split_clocks, split_mode)
     cfg = b.get_config()
-    assert cfg["split_groups"] > 0
+    assert cfg["split_groups"] > 0 and cfg["split_mode"] == split_mode
     out = b.run(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
     b.sync()
     _check(b, out, s)
@@ -98,10 +100,12 @@ def test_batch_rejects_bad_iv_length():
     assert ei.value.code == N.E_IVLEN
 
 
-def test_batched_workload_full_size_sampled():
+@pytest.mark.parametrize("split_mode", [N.BATCH_SPLIT_SHARED, N.BATCH_SPLIT_OWN])
+def test_batched_workload_full_size_sampled(split_mode):
     from paper_1909_04750_gb300.batch import Batch
     s = workloads.batched()
     b = Batch(s.n_bits, s.iv_lens)
+    b.set_config(4, 1, b.max_clocks // 64, split_mode)
     assert b.n == 100_000 and b.max_clocks == int(s.n_bits.max())
     out = b.run(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
     b.sync()
