@@ -321,9 +321,7 @@ cudaError_t capture(mickey_batch *b) {
     cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(uint32_t), cs);
     LoadArgs la{b->d_in, b->d_in + 10 * n, reinterpret_cast<const uint32_t *>(b->d_in + 20 * n),
                 n, b->d_perm, b->G, b->Gpad, b->d_scratch, b->d_err};
-    launch_load(la, cs);
-    PreclockArgs pa{b->d_scratch, b->d_state, b->G, b->Gpad};
-    launch_preclock(pa, cs);
+    launch_init(la, b->d_state, cs);
     const bool own = b->split_mode == MICKEY_BATCH_SPLIT_OWN && b->n_split;
     const uint32_t split_items = own ? 0u : b->n_split;
     BatchArgs ba{b->d_state, b->G, b->Gpad, b->d_slot, b->d_slot + 32 * size_t(b->Gpad),

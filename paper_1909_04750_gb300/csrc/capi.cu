@@ -206,9 +206,7 @@ int run_init(mickey_streams *s, const void *keys, const void *ivs,
     dl = iv_lens;
   }
   LoadArgs la{dk, di, dl, n, nullptr, s->G, s->Gpad, s->d_scratch, s->d_err};
-  CUDA_TRY(launch_load(la, s->stream), "load_kernel launch");
-  PreclockArgs pa{s->d_scratch, s->d_state, s->G, s->Gpad};
-  CUDA_TRY(launch_preclock(pa, s->stream), "preclock_kernel launch");
+  CUDA_TRY(launch_init(la, s->d_state, s->stream), "init_kernel launch");
   std::fill(s->pos.begin(), s->pos.end(), 0);
   return ok();
 }

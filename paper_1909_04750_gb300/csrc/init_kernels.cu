@@ -1,16 +1,22 @@
-// Key/IV loading for bitsliced MICKEY 2.0 (Sec. IV-A representation change,
-// Sec. IV-D input handler, and the cipher's initialisation).
+// Key/IV loading and preclocking for bitsliced MICKEY 2.0 (Sec. IV-A
+// representation change, Sec. IV-D input handler, and the cipher's
+// initialisation), in one kernel: one thread per 32-lane group.
 //
-// load_kernel      one thread per 32-lane group: reads the group's 32 keys,
-//                  IVs and IV lengths and turns them into bitsliced words
-//                  with 32x32 bit-matrix transposes (row-major -> column-
-//                  major, Sec. IV-A).  IVs are right-aligned per lane so that
-//                  all lanes of a group end their IV phase on the same clock;
-//                  a lane with a shorter IV is held still (masked) until its
-//                  first IV bit.
-// preclock_kernel  one thread per group: zero state, IV clocks, 80 key
-//                  clocks, 100 mixing preclocks, all in mixing mode; writes
-//                  the 200-word state.
+// Load    the group's 32 keys, IVs and IV lengths become bitsliced words by
+//         32x32 bit-matrix transposes (row-major -> column-major, Sec. IV-A),
+//         written to the group's column of the scratch rows.  IVs are
+//         right-aligned per lane so that all lanes of a group end their IV
+//         phase on the same clock; a lane with a shorter IV is held still
+//         (masked) until its first IV bit.
+// Preclock zero state, IV clocks, 80 key clocks, 100 mixing preclocks, all
+//         in mixing mode, reading the scratch words the same thread has just
+//         written; writes the 200-word state.
+// In one launch the loading of some warps (memory latency) overlaps the
+// clocking of others (logic issue).  When the instances are in their own
+// order (no permutation), a block first copies its 32 x kInitThreads keys,
+// IVs and IV lengths into shared memory with coalesced 4-byte cp.async
+// copies (all in flight at once), so that each thread reads its lanes'
+// 10-byte records from there instead of with scattered byte loads.
 #include "bitslice.cuh"
 #include "internal.h"
 
@@ -47,14 +53,52 @@ __device__ __forceinline__ uint32_t shift96_word(uint32_t w0, uint32_t w1,
   return __funnelshift_r(lo, hi, bs);
 }
 
-// Instance held by lane slot `slot` (32g + l).
-__device__ __forceinline__ uint64_t inst(const LoadArgs &a, uint64_t slot) {
-  return a.perm ? uint64_t(a.perm[slot]) : slot;
+// Shared-memory staging of a block's inputs (instances in their own order):
+// thread t's 32 ten-byte keys as words 81t .. 81t+79 (one spare word, so
+// that the rows of a warp's threads start in different banks), the same for
+// the IVs, and its 32 IV lengths at 33t .. 33t+31.
+constexpr int kRecWords = 81;
+constexpr int kLenWords = 33;
+constexpr size_t kStageBytes = size_t(kInitThreads) * (2 * kRecWords + kLenWords) * 4;
+
+// Big-endian 32 bits at byte offset o of a staged 320-byte row (the bytes
+// past the row's end come from the spare word or the next row and are masked
+// off by the caller).
+__device__ __forceinline__ uint32_t staged_be32(const uint32_t *row, int o) {
+  const uint32_t w0 = row[o >> 2], w1 = row[(o >> 2) + 1];
+  return __byte_perm(__funnelshift_r(w0, w1, 8 * (o & 3)), 0u, 0x0123);
 }
 
-__global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.G) return;
+// Where one group's inputs come from: the staged rows of its thread, or
+// global memory (through the permutation, if any).
+struct Src {
+  const LoadArgs *a;
+  uint64_t base;          // slot of lane 0
+  const uint32_t *krow;   // staged: 80 key words of this thread (else nullptr)
+  const uint32_t *vrow;   // staged IV words
+  const uint32_t *lrow;   // staged IV lengths
+  __device__ uint64_t inst(int l) const {
+    return a->perm ? uint64_t(a->perm[base + l]) : base + l;
+  }
+  // chunk q (q = 0, 1: 32 bits; q = 2: the last 16 bits, in the high half)
+  // of lane l's key or IV, big-endian
+  __device__ uint32_t chunk(bool iv, int l, int q) const {
+    if (krow) {
+      const uint32_t v = staged_be32(iv ? vrow : krow, 10 * l + 4 * q);
+      return q < 2 ? v : v & 0xFFFF0000u;
+    }
+    const uint8_t *p = (iv ? a->ivs : a->keys) + inst(l) * 10 + 4 * q;
+    return q < 2 ? load_be32(p) : (uint32_t(p[0]) << 24) | (uint32_t(p[1]) << 16);
+  }
+  __device__ uint32_t iv_len(int l) const {
+    if (lrow) return lrow[l];
+    return a->iv_lens ? a->iv_lens[inst(l)] : 80u;
+  }
+};
+
+// The load of group g: bitsliced key rows, right-aligned IV rows, activity
+// rows (mixed IV lengths only) and the info word.
+__device__ __forceinline__ void load_group(const LoadArgs &a, uint32_t g, const Src &src) {
   const uint64_t base = 32ull * g;
   const uint64_t left = a.n - base;
   const int nv = left >= 32 ? 32 : int(left);
@@ -65,7 +109,7 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
   for (int l = 0; l < 32; ++l) {
     int v = 0;
     if (l < nv) {
-      v = a.iv_lens ? int(min(a.iv_lens[inst(a, base + l)], 1000u)) : 80;
+      v = int(min(src.iv_len(l), 1000u));
       if (v > 80) {
         atomicOr(a.err, kErrIvLen);
         v = 80;
@@ -75,7 +119,7 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
     }
     len[l] = v;
   }
-  // The IV phase runs a multiple of 4 clocks (the preclock loop handles four
+  // The IV phase runs a multiple of 4 clocks (the preclock loop handles two
   // clocks per iteration); lanes are right-aligned to that length.
   const int phase = (max_len + 3) & ~3;
 #pragma unroll
@@ -90,12 +134,7 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int l = 31 - r;  // row r = lane 31-r, so result bit l = lane l
-      uint32_t w = 0;
-      if (l < nv) {
-        const uint8_t *p = a.keys + inst(a, base + l) * 10 + 4 * q;
-        w = q < 2 ? load_be32(p) : (uint32_t(p[0]) << 24) | (uint32_t(p[1]) << 16);
-      }
-      m[r] = w;
+      m[r] = l < nv ? src.chunk(false, l, q) : 0u;
     }
     transpose32(m);
 #pragma unroll
@@ -118,11 +157,9 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
       const int sft = phase - L;
       uint32_t w = 0;
       if (l < nv && L > 0) {
-        const uint8_t *p = a.ivs + inst(a, base + l) * 10;
-        const uint32_t w0 = load_be32(p) & prefix_mask(L, 0);
-        const uint32_t w1 = load_be32(p + 4) & prefix_mask(L, 1);
-        const uint32_t w2 =
-            ((uint32_t(p[8]) << 24) | (uint32_t(p[9]) << 16)) & prefix_mask(L, 2);
+        const uint32_t w0 = src.chunk(true, l, 0) & prefix_mask(L, 0);
+        const uint32_t w1 = src.chunk(true, l, 1) & prefix_mask(L, 1);
+        const uint32_t w2 = src.chunk(true, l, 2) & prefix_mask(L, 2);
         w = shift96_word(w0, w1, w2, sft, q);
       }
       m[r] = w;
@@ -139,18 +176,19 @@ __global__ void __launch_bounds__(kInitThreads) load_kernel(LoadArgs a) {
       }
     }
   }
-  a.scratch[size_t(kScratchRows) * a.Gpad + g] =
-      uint32_t(phase) | (mixed ? 0x100u : 0u);
+  a.scratch[size_t(kScratchRows) * a.Gpad + g] = uint32_t(phase) | (mixed ? 0x100u : 0u);
 }
 
 constexpr int kPre = 2;  // clocks per loop iteration (IV phase is a multiple of 4)
 
+// The preclock of group g from its scratch column (written by this thread).
 // kPre clocks per loop iteration: with a single clock per iteration the
 // shift of both registers makes every loop-carried word change register,
-// which costs copies and spills.
-__global__ void __launch_bounds__(kInitThreads) preclock_kernel(PreclockArgs a) {
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.G) return;
+// which costs copies and spills.  The IV (unless lanes are masked), key and
+// preclock phases share one loop body, the clock's input word chosen by its
+// index: one copy of the clock's code, so that warps in different phases
+// fetch the same instructions.
+__device__ __forceinline__ void preclock_group(const LoadArgs &a, uint32_t *state, uint32_t g) {
   uint32_t r[kReg], s[kReg];
 #pragma unroll
   for (int i = 0; i < kReg; ++i) r[i] = s[i] = 0u;
@@ -161,6 +199,7 @@ __global__ void __launch_bounds__(kInitThreads) preclock_kernel(PreclockArgs a) 
   const uint32_t *col = a.scratch + g;
   const size_t P = a.Gpad;
 
+  int c0 = 0;
   if (mixed) {
 #pragma unroll 1
     for (int c = 0; c < phase; c += kPre) {
@@ -168,25 +207,24 @@ __global__ void __launch_bounds__(kInitThreads) preclock_kernel(PreclockArgs a) 
       for (int u = 0; u < kPre; ++u)
         clock_kg<true, true>(r, s, col[(kIvRow + c + u) * P], col[(kActRow + c + u) * P]);
     }
-  } else {
+    c0 = phase;
+  }
+  // clock c: IV bit c (c < phase), key bit c - phase (c < phase + 80), else
+  // 0; one load per clock, of row 0 when the clock takes no input
+  const int end = phase + 180;
 #pragma unroll 1
-    for (int c = 0; c < phase; c += kPre) {
+  for (int c = c0; c < end; c += kPre) {
 #pragma unroll
-      for (int u = 0; u < kPre; ++u) clock_kg<true, false>(r, s, col[(kIvRow + c + u) * P], 0u);
+    for (int u = 0; u < kPre; ++u) {
+      const int cc = c + u;
+      const bool has = cc < phase + 80;
+      const int row = !has ? 0 : cc < phase ? kIvRow + cc : kKeyRow + cc - phase;
+      const uint32_t v = col[size_t(row) * P];
+      clock_kg<true, false>(r, s, has ? v : 0u, 0u);
     }
   }
-#pragma unroll 1
-  for (int j = 0; j < 80; j += kPre) {
-#pragma unroll
-    for (int u = 0; u < kPre; ++u) clock_kg<true, false>(r, s, col[(kKeyRow + j + u) * P], 0u);
-  }
-#pragma unroll 1
-  for (int c = 0; c < 100; c += kPre) {
-#pragma unroll
-    for (int u = 0; u < kPre; ++u) clock_kg<true, false>(r, s, 0u, 0u);
-  }
 
-  uint32_t *st = a.state + g;
+  uint32_t *st = state + g;
 #pragma unroll
   for (int i = 0; i < kReg; ++i) {
     st[size_t(i) * P] = r[i];
@@ -194,17 +232,79 @@ __global__ void __launch_bounds__(kInitThreads) preclock_kernel(PreclockArgs a) 
   }
 }
 
-}  // namespace
-
-cudaError_t launch_load(const LoadArgs &a, cudaStream_t st) {
-  const uint32_t blocks = (a.G + kInitThreads - 1) / kInitThreads;
-  load_kernel<<<blocks, kInitThreads, 0, st>>>(a);
-  return cudaGetLastError();
+// Copy `bytes` bytes from global src to the staged rows at dst: byte b of
+// the source goes to row b / row_bytes, offset b % row_bytes, rows
+// stride_words apart.  When src is 4-byte aligned the words go by cp.async
+// (global to shared without a register round trip, all of a thread's copies
+// in flight at once; the caller waits for them); otherwise byte loads.
+__device__ __forceinline__ void stage_rows(const uint8_t *src, uint64_t bytes, uint32_t *dst,
+                                           int row_bytes, int stride_words) {
+  const uint32_t t = threadIdx.x;
+  const int row_words = row_bytes / 4;
+  if ((reinterpret_cast<uintptr_t>(src) & 3u) == 0) {
+    const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src);
+    const uint64_t words = bytes / 4;
+    for (uint64_t w = t; w < words; w += kInitThreads) {
+      const uint32_t d = uint32_t(__cvta_generic_to_shared(
+          dst + (w / row_words) * stride_words + w % row_words));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(s4 + w) : "memory");
+    }
+    // a last partial word (byte copies into the row's word)
+    if (t == 0 && (bytes & 3)) {
+      uint32_t v = 0;
+      for (uint64_t b = words * 4; b < bytes; ++b) v |= uint32_t(src[b]) << (8 * (b & 3));
+      dst[(words / row_words) * stride_words + words % row_words] = v;
+    }
+  } else {
+    for (uint64_t w = t; w * 4 < bytes; w += kInitThreads) {
+      uint32_t v = 0;
+      for (int b = 0; b < 4 && w * 4 + b < bytes; ++b) v |= uint32_t(src[w * 4 + b]) << (8 * b);
+      dst[(w / row_words) * stride_words + w % row_words] = v;
+    }
+  }
 }
 
-cudaError_t launch_preclock(const PreclockArgs &a, cudaStream_t st) {
+template <bool STAGED>
+__global__ void __launch_bounds__(kInitThreads) init_kernel(LoadArgs a, uint32_t *state) {
+  extern __shared__ uint32_t stage[];
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  Src src{&a, 32ull * g, nullptr, nullptr, nullptr};
+  if constexpr (STAGED) {
+    // the block's instances, in their own order: keys, IVs, IV lengths
+    const uint64_t first = 32ull * blockIdx.x * kInitThreads;
+    const uint64_t count = min(uint64_t(32) * kInitThreads, a.n - first);
+    uint32_t *ks = stage, *vs = stage + kInitThreads * kRecWords;
+    uint32_t *ls = vs + kInitThreads * kRecWords;
+    stage_rows(a.keys + first * 10, count * 10, ks, 320, kRecWords);
+    stage_rows(a.ivs + first * 10, count * 10, vs, 320, kRecWords);
+    if (a.iv_lens)
+      stage_rows(reinterpret_cast<const uint8_t *>(a.iv_lens + first), count * 4, ls, 128,
+                 kLenWords);
+    else
+      for (uint32_t i = threadIdx.x; i < kInitThreads * kLenWords; i += kInitThreads) ls[i] = 80u;
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    src.krow = ks + threadIdx.x * kRecWords;
+    src.vrow = vs + threadIdx.x * kRecWords;
+    src.lrow = ls + threadIdx.x * kLenWords;
+  }
+  if (g >= a.G) return;
+  load_group(a, g, src);
+  preclock_group(a, state, g);
+}
+
+}  // namespace
+
+cudaError_t launch_init(const LoadArgs &a, uint32_t *state, cudaStream_t st) {
   const uint32_t blocks = (a.G + kInitThreads - 1) / kInitThreads;
-  preclock_kernel<<<blocks, kInitThreads, 0, st>>>(a);
+  if (a.perm) {
+    init_kernel<false><<<blocks, kInitThreads, 0, st>>>(a, state);
+  } else {
+    const cudaError_t e = cudaFuncSetAttribute(
+        init_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kStageBytes));
+    if (e != cudaSuccess) return e;
+    init_kernel<true><<<blocks, kInitThreads, kStageBytes, st>>>(a, state);
+  }
   return cudaGetLastError();
 }
 

@@ -39,14 +39,10 @@ struct LoadArgs {
   int *err;
 };
 
-struct PreclockArgs {
-  const uint32_t *scratch;
-  uint32_t *state;          // kStateRows * Gpad words
-  uint32_t G, Gpad;
-};
-
-cudaError_t launch_load(const LoadArgs &a, cudaStream_t st);
-cudaError_t launch_preclock(const PreclockArgs &a, cudaStream_t st);
+// Key/IV loading and preclocking of every group (init_kernels.cu): the
+// scratch rows of `a`, then the 200-word state into `state` (kStateRows *
+// Gpad words).
+cudaError_t launch_init(const LoadArgs &a, uint32_t *state, cudaStream_t st);
 
 struct KeystreamArgs {
   uint32_t *state;          // kStateRows * Gpad words, read and written back

@@ -131,9 +131,7 @@ extern "C" MICKEY_API int mickey_init_state_noalloc(const uint8_t *keys, const u
     lens = reinterpret_cast<const uint32_t *>(in + n * 20);
   }
   LoadArgs la{in, in + n * 10, lens, n, nullptr, G, Gpad, rows, err};
-  if (launch_load(la, st) != cudaSuccess) return set_error(MICKEY_E_CUDA, "load_kernel launch");
-  PreclockArgs pa{rows, state, G, Gpad};
-  if (launch_preclock(pa, st) != cudaSuccess)
-    return set_error(MICKEY_E_CUDA, "preclock_kernel launch");
+  if (launch_init(la, state, st) != cudaSuccess)
+    return set_error(MICKEY_E_CUDA, "init_kernel launch");
   return set_error(MICKEY_OK, "");
 }
