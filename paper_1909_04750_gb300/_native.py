@@ -89,6 +89,15 @@ SIGNATURES = {
     "mickey_server_free": (None, [c_void_p]),
     "mickey_init_state_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p,
                                           c_void_p]),
+    "grain_init_streams": (c_void_p, [c_void_p, c_void_p, c_size_t, c_int, c_void_p]),
+    "grain_generate": (c_int, [c_void_p, c_uint64, c_void_p, c_int]),
+    "grain_output_bytes": (c_size_t, [c_size_t, c_uint64, c_int]),
+    "grain_set_stream": (c_int, [c_void_p, c_void_p]),
+    "grain_sync": (c_int, [c_void_p]),
+    "grain_position": (c_uint64, [c_void_p]),
+    "grain_export_state": (c_int, [c_void_p, c_void_p]),
+    "grain_ops_per_clock": (c_int, [c_int]),
+    "grain_free": (None, [c_void_p]),
 }
 
 

@@ -126,6 +126,35 @@ def batched(n: int | None = None) -> StreamSet:
 
 
 # --------------------------------------------------------------------------
+# Grain (the paper's second stream cipher): 80-bit keys, 64-bit IVs
+# --------------------------------------------------------------------------
+
+GRAIN_SCALE = dict(name="grain_scale", seed=6, n=1 << 20, n_bits=1 << 14)
+
+
+@dataclass
+class GrainSet:
+    name: str
+    seed: int
+    keys: np.ndarray          # uint8 [n, 10]
+    ivs: np.ndarray           # uint8 [n, 8]
+
+    @property
+    def n(self) -> int:
+        return int(self.keys.shape[0])
+
+
+def grain_streams(n: int | None = None, seed: int = GRAIN_SCALE["seed"]) -> GrainSet:
+    """Instance i takes draws 3i .. 3i+2 of splitmix64(seed): key = the
+    little-endian bytes of draw 0 and bytes 0-1 of draw 1, IV = the 8
+    little-endian bytes of draw 2."""
+    n = GRAIN_SCALE["n"] if n is None else n
+    d = splitmix64(seed, 3 * n).reshape(n, 3)
+    return GrainSet("grain_scale", seed, _ten_bytes(d[:, 0], d[:, 1]),
+                    d[:, 2].astype("<u8").view(np.uint8).reshape(n, 8).copy())
+
+
+# --------------------------------------------------------------------------
 # served workload: a request trace
 # --------------------------------------------------------------------------
 

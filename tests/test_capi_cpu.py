@@ -26,7 +26,8 @@ def declared_symbols():
     for h in os.listdir(os.path.join(ROOT, "include")):
         if h.endswith(".h"):
             text = open(os.path.join(ROOT, "include", h)).read()
-            names |= set(re.findall(r"MICKEY_API[^;{]*?\b(mickey_\w+)\s*\(", text, re.S))
+            names |= set(re.findall(r"MICKEY_API[^;{]*?\b((?:mickey|grain)_\w+)\s*\(", text,
+                                    re.S))
     return sorted(names)
 
 
@@ -208,3 +209,12 @@ def test_packed_offsets_match_library_sizes(L):
         else:
             last = 4 * int(nb[64:].max())
             assert int(offs[-1]) + last == total
+
+
+def test_grain_ops_per_clock(L):
+    # output 11 (7 NFSR taps and the 5-input filter), LFSR 3 (6 taps),
+    # NFSR 24 (12 linear terms, 11 products); an init clock adds z once more
+    assert L.grain_ops_per_clock(0) == 38
+    assert L.grain_ops_per_clock(1) == 39
+    assert not L.grain_init_streams(None, None, 4, N.MEM_HOST, None)
+    assert L.mickey_last_error() == N.E_ARG
