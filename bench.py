@@ -34,12 +34,12 @@ WORKLOAD = ("plain_scale: 2^20 MICKEY 2.0 instances (32768 bitsliced groups), 80
 
 # DRAM traffic of one keystream launch of the plain workload at scale
 # (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu capture of the
-# full-size launch in the autotuned configuration: 86.6 MB read + 2.189 GB
+# full-size launch in the autotuned configuration: 86.5 MB read + 2.190 GB
 # written; algorithmic 2.20 GB = 2 GiB of output + the 26.2 MB state read
 # and written).  It stands for the kernel sources it was measured on (their
 # digest) and that launch configuration only; otherwise traffic is null.
-KEYSTREAM_TRAFFIC = {"digest": "9321f55be9be5d8a", "launch": "persistent, 4 clocks/step, staged rows",
-                     "bytes_per_launch": 2275657472}
+KEYSTREAM_TRAFFIC = {"digest": "b222b2fba8f6fc98", "launch": "persistent, 4 clocks/step, staged rows",
+                     "bytes_per_launch": 2276071936}
 
 
 def parse():
@@ -216,6 +216,18 @@ def verify_served(srv, reqs, keyset, k: int = 96, max_bits: int = 1 << 21) -> di
                     "state after the same keystream bits"}
 
 
+def verify_grain(s, out, n_bits: int = 1 << 14, k: int = 1024) -> dict:
+    """Sampled rows of the last Grain bytes step against the Grain oracle."""
+    from oracle import grain as og
+    import torch
+    idx = _sample_rows(s.n, k)
+    got = out[torch.from_numpy(idx).to(out.device)].cpu().numpy()
+    ref = og.batch_bytes(s.keys[idx], s.ivs[idx], n_bits, threads=os.cpu_count() or 1)
+    return {"rows": int(idx.size), "ok": bool(np.array_equal(got, ref)),
+            "what": "row-major bytes of sampled Grain instances (first and last group "
+                    "included) of the last timed step == scalar Grain oracle"}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -362,8 +374,9 @@ def main():
     # multi-GPU run for minutes)
     extras = {}
     if world == 1 and not args.no_extras:
-        from paper_1909_04750_gb300 import bench_batched, bench_fused, bench_served
+        from paper_1909_04750_gb300 import bench_batched, bench_fused, bench_grain, bench_served
         extras["fused"] = bench_fused.measure(peak=pk, verify=verify_fused)
+        extras["grain"] = bench_grain.measure(peak=pk, verify=verify_grain)
         extras["batched"] = bench_batched.measure(plain_gbit_s=value, verify=verify_batched)
         extras["served"] = bench_served.measure(duration=args.served_duration,
                                                 plain_gbit_s=value, verify=verify_served)

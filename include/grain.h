@@ -41,6 +41,11 @@ typedef struct grain_streams grain_streams;
 MICKEY_API grain_streams *grain_init_streams(const void *keys, const void *ivs, size_t n, int mem,
                                              void *cuda_stream);
 
+/* Re-key the handle in place (same n, no device allocation after the
+ * first call with host inputs): loading and the 160 initialisation clocks
+ * again; the position returns to 0. */
+MICKEY_API int grain_reset_streams(grain_streams *s, const void *keys, const void *ivs, int mem);
+
 /* The next n_bits keystream bits of every instance (1 .. 2^34 per call) into
  * the caller-owned DEVICE buffer `out` (grain_output_bytes bytes).  Stateful:
  * each call continues every stream.  Errors: MICKEY_E_ARG, MICKEY_E_LAYOUT

@@ -90,6 +90,7 @@ SIGNATURES = {
     "mickey_init_state_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_size_t, c_void_p,
                                           c_void_p]),
     "grain_init_streams": (c_void_p, [c_void_p, c_void_p, c_size_t, c_int, c_void_p]),
+    "grain_reset_streams": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "grain_generate": (c_int, [c_void_p, c_uint64, c_void_p, c_int]),
     "grain_output_bytes": (c_size_t, [c_size_t, c_uint64, c_int]),
     "grain_set_stream": (c_int, [c_void_p, c_void_p]),

@@ -466,6 +466,29 @@ MICKEY_API grain_streams *grain_init_streams(const void *keys, const void *ivs, 
   return s;
 }
 
+MICKEY_API int grain_reset_streams(grain_streams *s, const void *keys, const void *ivs, int mem) {
+  if (!s || !keys || !ivs || (mem != MICKEY_MEM_HOST && mem != MICKEY_MEM_DEVICE))
+    return grain_fail(MICKEY_E_ARG, "NULL argument or bad memory kind");
+  const size_t n = s->n;
+  const uint8_t *dk = static_cast<const uint8_t *>(keys), *dv = static_cast<const uint8_t *>(ivs);
+  if (mem == MICKEY_MEM_HOST) {
+    if (!s->d_inputs && cudaMalloc(&s->d_inputs, n * 18) != cudaSuccess)
+      return grain_fail(MICKEY_E_OOM, "input staging");
+    if (cudaMemcpyAsync(s->d_inputs, keys, n * 10, cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(s->d_inputs + n * 10, ivs, n * 8, cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess)
+      return grain_fail(MICKEY_E_CUDA, "key/IV upload");
+    dk = s->d_inputs;
+    dv = s->d_inputs + n * 10;
+  }
+  GrainInitArgs ia{dk, dv, n, s->G, s->Gpad, s->d_state};
+  grain_init_kernel<<<(s->G + kInitT - 1) / kInitT, kInitT, 0, s->stream>>>(ia);
+  if (cudaGetLastError() != cudaSuccess) return grain_fail(MICKEY_E_CUDA, "grain init launch");
+  s->pos = 0;
+  return set_error(MICKEY_OK, "");
+}
+
 MICKEY_API int grain_generate(grain_streams *s, uint64_t n_bits, void *out, int layout) {
   if (!s || !out || n_bits == 0) return grain_fail(MICKEY_E_ARG, "NULL argument or n_bits == 0");
   if (n_bits > kMaxBitsPerCall) return grain_fail(MICKEY_E_ARG, "n_bits per call is limited to 2^34");

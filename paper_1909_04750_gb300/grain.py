@@ -56,6 +56,18 @@ class GrainStreams:
         N.check(self._L.grain_generate(self._h, n_bits, ctypes.c_void_p(out.data_ptr()), lay))
         return out
 
+    def reset(self, keys, ivs):
+        """Re-key every instance in place (device tensors or host arrays)."""
+        if isinstance(keys, torch.Tensor) and keys.is_cuda:
+            k, v, mem = keys.contiguous(), ivs.contiguous(), N.MEM_DEVICE
+            kp, vp = k.data_ptr(), v.data_ptr()
+        else:
+            k, v = np.ascontiguousarray(keys, np.uint8), np.ascontiguousarray(ivs, np.uint8)
+            kp, vp, mem = k.ctypes.data, v.ctypes.data, N.MEM_HOST
+        self._keep = (k, v)
+        self._L.grain_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream))
+        N.check(self._L.grain_reset_streams(self._h, kp, vp, mem))
+
     def sync(self):
         N.check(self._L.grain_sync(self._h))
 

@@ -101,3 +101,18 @@ def test_rejections():
         N.E_LAYOUT
     assert L.grain_generate(st._h, 0, ctypes.c_void_p(out.data_ptr()), N.LAYOUT_BYTES) == N.E_ARG
     assert st.position() == 0
+
+
+def test_reset_rekeys_in_place():
+    a = workloads.grain_streams(64, seed=14)
+    b = workloads.grain_streams(64, seed=15)
+    st = _gs(a)
+    st.generate(333, "bytes")
+    st.reset(b.keys, b.ivs)                          # host inputs
+    assert st.position() == 0
+    got = st.generate(500, "bytes").cpu().numpy()
+    st.reset(torch.from_numpy(a.keys).cuda(), torch.from_numpy(a.ivs).cuda())
+    again = st.generate(500, "bytes").cpu().numpy()
+    st.sync()
+    assert np.array_equal(got, og.batch_bytes(b.keys, b.ivs, 500, threads=THREADS))
+    assert np.array_equal(again, og.batch_bytes(a.keys, a.ivs, 500, threads=THREADS))
