@@ -6,7 +6,7 @@
 A step re-keys every instance (loading + 160 initialisation clocks) and
 generates 2^14 bits of each, as row-major bytes (2 GiB) or in the bitsliced
 layout.  Prints one JSON line: keystream Gbit/s of whole steps, and the
-keystream kernel's integer-logic roofline fraction (38 logic ops per clock
+keystream kernel's integer-logic roofline fraction (37 logic ops per clock
 per 32-lane group over its CUDA-event time).
 """
 import argparse

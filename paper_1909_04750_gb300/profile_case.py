@@ -26,6 +26,9 @@ instances x ``n_bits``, ``--reps`` times.
 own length in one mickey_generate_ragged call, ``--reps`` times: every
 length ``n_bits`` (``--spread 0``) or uniform in [n_bits - spread, n_bits].
 
+``grain``: n Grain instances (seed 6) generate ``n_bits`` each in ``layout``
+(bitsliced or bytes), ``--reps`` times.
+
 ``serve``: a server holding n streams serves one request of ``n_bits`` bits
 per stream ``--reps`` times, each in one step of split groups only (the
 split kernel launches one warp per group, so its counters come from the
@@ -47,7 +50,7 @@ def main():
     p.add_argument("--layout", default="bytes")
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--case", choices=("plain", "split", "serve", "crc8", "batched", "lfsr",
-                                      "ragged"), default="plain")
+                                      "ragged", "grain"), default="plain")
     p.add_argument("--spread", type=int, default=0)
     p.add_argument("--autotune", action="store_true")
     a = p.parse_args()
@@ -94,6 +97,16 @@ def main():
             srv.run(reqs, realtime=False)
         torch.cuda.synchronize()
         srv.free()
+        print("ok", vars(a))
+        return
+    if a.case == "grain":
+        from .grain import GrainStreams
+        s = workloads.grain_streams(a.n)
+        st = GrainStreams(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
+        out = None
+        for _ in range(a.reps):
+            out = st.generate(a.n_bits, a.layout, out=out)
+        st.sync()
         print("ok", vars(a))
         return
     if a.case == "ragged":

@@ -213,8 +213,8 @@ def test_packed_offsets_match_library_sizes(L):
 
 def test_grain_ops_per_clock(L):
     # output 11 (7 NFSR taps and the 5-input filter), LFSR 3 (6 taps),
-    # NFSR 24 (12 linear terms, 11 products); an init clock adds z once more
-    assert L.grain_ops_per_clock(0) == 38
-    assert L.grain_ops_per_clock(1) == 39
+    # NFSR 23 (12 linear terms, 11 products); an init clock adds z once more
+    assert L.grain_ops_per_clock(0) == 37
+    assert L.grain_ops_per_clock(1) == 38
     assert not L.grain_init_streams(None, None, 4, N.MEM_HOST, None)
     assert L.mickey_last_error() == N.E_ARG
