@@ -213,13 +213,18 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
  *           tiles deep; with too few warp-groups it runs as PERSISTENT);
  *           MICKEY_MODE_AUTO: as PERSISTENT.
  *   unroll  clocks per inner step, 2 or 4.
- *   stage   row layouts: stage each row's words of several tiles in shared
- *           memory and write 16- or 32-byte chunks (four tiles for GRID and
- *           PERSISTENT2, eight for PERSISTENT; used when n_bits is a multiple
- *           of 32 x that depth and the output 16-byte aligned).
+ *   stage   the output tile of the row layouts: 0 writes each 32-clock tile's
+ *           4 bytes per row directly; otherwise each row's words of several
+ *           tiles are staged in shared memory and written as one chunk of
+ *           4 x depth bytes -- 1: the mode's default depth (8 tiles for
+ *           PERSISTENT, 4 for GRID and PERSISTENT2); 2, 4, 8: that depth
+ *           (PERSISTENT: 2, 4 or 8; GRID: 2 or 4; PERSISTENT2: 4).  Used when
+ *           n_bits is a multiple of 32 x depth and the output 16-byte
+ *           aligned, else the row stores are direct.
  * Environment, read when a handle is created: MICKEY_MODE (grid,
  * persistent, persistent2), MICKEY_UNROLL (2, 4), MICKEY_STAGE (0, 1) and
- * MICKEY_PERSIST_BLOCKS (fewer persistent blocks than SMs) set the defaults;
+ * MICKEY_PERSIST_BLOCKS (fewer persistent blocks than SMs) set the defaults
+ * (MICKEY_STAGE takes 0, 1, 2, 4 or 8 as above);
  * MICKEY_SPIN_LIMIT bounds a persistent tail piece's wait for its head
  * (polls of about 256 ns, default 2^24), after which mickey_sync reports
  * MICKEY_E_TIMEOUT and that call's output and state are undefined;
@@ -233,8 +238,8 @@ MICKEY_API mickey_streams *mickey_import_state(const uint8_t *states,
 #define MICKEY_MODE_PERSISTENT2 3
 
 typedef struct {
-  int mode, unroll, stage;
-  float ms; /* best of two timed launches */
+  int mode, unroll, stage; /* stage: 0 direct, else the staging depth in tiles */
+  float ms;                /* best of two timed launches */
 } mickey_tune_result;
 
 MICKEY_API int mickey_set_config(mickey_streams *s, int layout, int mode, int unroll,
@@ -242,7 +247,8 @@ MICKEY_API int mickey_set_config(mickey_streams *s, int layout, int mode, int un
 MICKEY_API int mickey_get_config(const mickey_streams *s, int layout, int *mode,
                                  int *unroll, int *stage);
 
-/* Time every configuration on this handle's own streams for one call of
+/* Time every configuration (mode x unroll x output tile: up to 20
+ * candidates) on this handle's own streams for one call of
  * n_bits in `layout` (the state is saved and restored: positions do not
  * move), keep the fastest for that layout, and report each candidate in
  * results[0 .. min(max_results, *n_results)).  Synchronous; allocates a

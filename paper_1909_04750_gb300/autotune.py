@@ -1,9 +1,11 @@
 """Autotuner for the keystream kernel's launch configuration.
 
 For a (GPU, instance count, bits per call, layout) the library's
-``mickey_tune`` times every compiled configuration -- grid or persistent
-launch, 2 or 4 clocks per inner step, staged or direct row stores -- on the
-handle's own streams (state saved and restored) and keeps the fastest.  The
+``mickey_tune`` times every compiled configuration -- grid, paired or
+two-block persistent launch, 2 or 4 clocks per inner step, and the output
+tile: direct 4-byte row stores or rows staged 2, 4 or 8 tiles deep (8-, 16-
+or 32-byte row chunks) -- on the handle's own streams (state saved and
+restored) and keeps the fastest.  The
 choice is cached in a JSON file next to the built library so later handles
 of the same shape reuse it without timing.
 """
@@ -60,9 +62,9 @@ def tune(streams, n_bits: int, layout: int, refresh: bool = False) -> dict:
     if hit is not None:
         N.check(L.mickey_set_config(streams._h, layout, hit["mode"], hit["unroll"], hit["stage"]))
         return hit
-    res = (N.TuneResult * 16)()
+    res = (N.TuneResult * 32)()
     count = ctypes.c_int(0)
-    N.check(L.mickey_tune(streams._h, n_bits, layout, res, 16, ctypes.byref(count)))
+    N.check(L.mickey_tune(streams._h, n_bits, layout, res, 32, ctypes.byref(count)))
     cands = [{"mode": MODE_NAMES[r.mode], "unroll": r.unroll, "stage": r.stage,
               "ms": float(r.ms)} for r in res[: count.value]]
     mode, unroll, stage = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -79,5 +81,9 @@ def tune(streams, n_bits: int, layout: int, refresh: bool = False) -> dict:
 
 
 def describe(entry: dict) -> str:
-    return "%s, %d clocks/step, %s rows" % (MODE_NAMES.get(entry["mode"], "?"), entry["unroll"],
-                                             "staged" if entry["stage"] else "direct")
+    st = entry["stage"]
+    default = {N.MODE_PERSISTENT: 8, N.MODE_AUTO: 8}.get(entry["mode"], 4)
+    depth = default if st == 1 else st
+    rows = "direct rows" if not st else ("staged rows" if depth == default
+                                         else "rows staged %d tiles" % depth)
+    return "%s, %d clocks/step, %s" % (MODE_NAMES.get(entry["mode"], "?"), entry["unroll"], rows)

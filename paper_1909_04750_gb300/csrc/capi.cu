@@ -26,11 +26,12 @@ struct mickey_streams {
   cudaStream_t stream = nullptr;
   int unroll = 4;
   int mode = 0;                   // 0 auto, 1 grid, 2 persistent
-  bool stage = true;              // row layouts: 16-byte staged row stores
+  int stage = 1;                  // row layouts: 0 direct stores, 1 the mode's default
+                                  // staging depth, 2 / 4 / 8 that many tiles
   struct LayoutCfg {
     bool set = false;
     int mode = 0, unroll = 4;
-    bool stage = true;
+    int stage = 1;
   } cfg[4];                       // per-layout settings (mickey_set_config / tune)
   int sm_count = 0;
   int persist_blocks = 0;         // blocks of the persistent kernel (<= SMs)
@@ -145,7 +146,10 @@ int allocate(mickey_streams *s, size_t n) {
   s->pos.assign(n, 0);
   s->unroll = default_unroll();
   s->mode = default_mode();
-  if (const char *v = getenv("MICKEY_STAGE")) s->stage = atoi(v) != 0;
+  if (const char *v = getenv("MICKEY_STAGE")) {
+    const int d = atoi(v);
+    s->stage = (d == 0 || d == 1 || d == 2 || d == 4 || d == 8) ? d : 1;
+  }
   if (const char *v = getenv("MICKEY_SPIN_LIMIT")) {
     const long long l = atoll(v);
     if (l > 0 && l < (1ll << 31)) s->spin_limit = uint32_t(l);
@@ -256,7 +260,7 @@ int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
   const auto &c = s->cfg[layout];
   int mode = c.set ? c.mode : s->mode;
   const int unroll = c.set ? c.unroll : s->unroll;
-  const bool stage = c.set ? c.stage : s->stage;
+  const int stage = c.set ? c.stage : s->stage;
   if (mode == MICKEY_MODE_GRID) {
     CUDA_TRY(launch_keystream(ka, layout, unroll, stage, nullptr, s->stream),
              "keystream_kernel launch");
@@ -266,7 +270,9 @@ int launch_generate(mickey_streams *s, uint64_t bits, void *out, int layout) {
   const uint32_t per_sm = persist_per_sm(mode);
   const uint64_t W = (s->G + 31) / 32, NT = (bits + 31) / 32;
   PersistArgs pa;
-  pa.stage_tiles = per_sm == 2 ? 4u : 8u;
+  // the two-block kernel stages 4 tiles; the paired kernel 8 unless told otherwise
+  pa.paired = per_sm == 2 ? 0u : 1u;
+  pa.stage_tiles = per_sm == 2 ? 4u : (stage == 2 || stage == 4 ? uint32_t(stage) : 8u);
   pa.W = uint32_t(W);
   if (use_persistent(s, mode)) {
     const uint64_t slots = uint64_t(s->persist_blocks) * per_sm * 4;
@@ -629,11 +635,13 @@ int mickey_set_config(mickey_streams *s, int layout, int mode, int unroll, int s
   bool known = false;
   for (int k : kUnrolls) known |= (k == unroll);
   if (!known) return fail(MICKEY_E_ARG, "unroll %d is not compiled (2 or 4)", unroll);
+  if (stage != 0 && stage != 1 && stage != 2 && stage != 4 && stage != 8)
+    return fail(MICKEY_E_ARG, "stage must be 0, 1, 2, 4 or 8 (got %d)", stage);
   auto &c = s->cfg[layout];
   c.set = true;
   c.mode = mode;
   c.unroll = unroll;
-  c.stage = stage != 0;
+  c.stage = stage;
   return ok();
 }
 
@@ -643,7 +651,7 @@ int mickey_get_config(const mickey_streams *s, int layout, int *mode, int *unrol
   const auto &c = s->cfg[layout];
   *mode = c.set ? c.mode : s->mode;
   *unroll = c.set ? c.unroll : s->unroll;
-  *stage = (c.set ? c.stage : s->stage) ? 1 : 0;
+  *stage = c.set ? c.stage : s->stage;
   return ok();
 }
 
@@ -679,13 +687,23 @@ int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout, mickey_tune_resu
   mickey_streams::LayoutCfg best = keep;
   for (int mode : {MICKEY_MODE_GRID, MICKEY_MODE_PERSISTENT, MICKEY_MODE_PERSISTENT2}) {
     if (mode == MICKEY_MODE_PERSISTENT2 && !use_persistent(s, mode)) continue;
+    // output tile: direct row stores, or rows staged this many tiles deep
+    // (the depths the mode's kernels are compiled for)
+    std::vector<int> stages{0};
+    if (row) {
+      const std::vector<int> depths = mode == MICKEY_MODE_GRID      ? std::vector<int>{2, 4}
+                                      : mode == MICKEY_MODE_PERSISTENT ? std::vector<int>{2, 4, 8}
+                                                                    : std::vector<int>{4};
+      for (int d : depths)
+        if (n_bits % (32 * uint64_t(d)) == 0) stages.push_back(d);
+    }
     for (int unroll : kUnrolls) {
-      for (int stage = 0; stage <= (row && n_bits % 128 == 0 ? 1 : 0); ++stage) {
+      for (int stage : stages) {
         auto &c = s->cfg[layout];
         c.set = true;
         c.mode = mode;
         c.unroll = unroll;
-        c.stage = stage != 0;
+        c.stage = stage;
         float ms = 1e30f;
         for (int rep = 0; rep < 2 && rc == MICKEY_OK; ++rep) {
           cudaMemcpyAsync(s->d_state, saved, st_sz, cudaMemcpyDeviceToDevice, s->stream);

@@ -75,7 +75,8 @@ struct PersistArgs {
   uint32_t blocks;      // grid: 1 or 2 blocks per SM (cooperative), or one block per
                         // 4 warp-groups (paired launch with L = NT, not cooperative)
   uint32_t cooperative; // 1: all blocks resident (needed when segments hand off)
-  uint32_t stage_tiles; // row staging depth: 8 (one block per SM) or 4 (two)
+  uint32_t stage_tiles; // row staging depth in tiles: 2, 4 or 8 (paired kernel), 4 (two-block)
+  uint32_t paired;      // 1: clock warps paired with emission warps; 0: two-block kernel
   uint32_t W;           // warp-groups = ceil(G / 32)
   uint64_t L;           // tiles of the work line per warp
   uint32_t *flags;      // W words
@@ -100,9 +101,11 @@ struct RaggedArgs {
 cudaError_t launch_ragged(const RaggedArgs &a, int layout, cudaStream_t st);
 
 // p == nullptr: grid mode (one thread per group); else persistent mode.
-// stage: row layouts stage four tiles per row and write 16-byte chunks
-// (used when n_bits % 128 == 0 and `out` is 16-byte aligned).
-cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll, bool stage,
+// stage: row layouts stage this many tiles per row (grid: 2 or 4; persistent:
+// p->stage_tiles) and write whole chunks of 4 x stage bytes per row, used when
+// n_bits is a multiple of 32 x stage and `out` is 16-byte aligned; 0: direct
+// 4-byte row stores.
+cudaError_t launch_keystream(const KeystreamArgs &a, int layout, int unroll, int stage,
                              const PersistArgs *p, cudaStream_t st);
 
 }  // namespace mickey

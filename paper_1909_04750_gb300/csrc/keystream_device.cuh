@@ -13,14 +13,19 @@ struct EmitCtx {
   uint32_t lane_mask;  // valid lanes of this group (last group may be partial)
   bool vec_ok;         // 16-byte vector stores allowed (bitsliced layout)
   bool word_ok;        // 4-byte row stores allowed (bytes layout)
-  bool stage;          // row layouts: stage ST tiles per row (16- or 32-byte stores)
+  bool stage;          // row layouts: stage ST tiles per row (8-, 16- or 32-byte stores)
 };
 
-// Launches of the persistent kernel (keystream_persistent.cuh), one
-// translation unit per staging depth: ST = 8 (one block per SM) and ST = 4
-// (two blocks per SM).
+// Launches of the persistent kernels (keystream_persistent.cuh), one
+// translation unit per kernel and staging depth: the paired clock/emission
+// kernel with ST = 8, 4 or 2 tiles (one block per SM), and the two-block
+// kernel with ST = 4.
 cudaError_t launch_persistent8(const KeystreamArgs &a, int layout, int unroll, const EmitCtx &e,
                                const PersistArgs &p, cudaStream_t st);
+cudaError_t launch_paired4(const KeystreamArgs &a, int layout, int unroll, const EmitCtx &e,
+                           const PersistArgs &p, cudaStream_t st);
+cudaError_t launch_paired2(const KeystreamArgs &a, int layout, int unroll, const EmitCtx &e,
+                           const PersistArgs &p, cudaStream_t st);
 cudaError_t launch_persistent4(const KeystreamArgs &a, int layout, int unroll, const EmitCtx &e,
                                const PersistArgs &p, cudaStream_t st);
 
@@ -132,7 +137,8 @@ __device__ __forceinline__ void emit_tile(uint32_t *z, uint32_t *rb, const Keyst
 
 // Row layouts with staging: write the staged words of tiles tA..tB (one
 // aligned block of ST tiles, or part of one) of every valid row; a whole
-// block goes out as ST/4 16-byte stores per row (and per f32 row).
+// block goes out as ST/4 16-byte stores per row (one 8-byte store for
+// ST = 2), and the same for the f32 row.
 template <int LAYOUT, int ST>
 __device__ __forceinline__ void flush_rows(const uint32_t *rb, const KeystreamArgs &a,
                                            uint32_t g, uint32_t tA, uint32_t tB,
@@ -146,7 +152,16 @@ __device__ __forceinline__ void flush_rows(const uint32_t *rb, const KeystreamAr
     if (!((e.lane_mask >> l) & 1u)) continue;
     const uint32_t *src = rb + l * (kKsThreads * ST);
     uint8_t *o = base + uint64_t(uint32_t(l) * pitch);
-    if (n == ST) {
+    if (ST == 2 && n == ST) {
+      const uint2 v = *reinterpret_cast<const uint2 *>(src);
+      *reinterpret_cast<uint2 *>(o) = v;
+      if constexpr (LAYOUT == MICKEY_LAYOUT_U32_F32) {
+        float2 f;
+        f.x = __uint2float_rn(v.x >> 8) * 0x1p-24f;
+        f.y = __uint2float_rn(v.y >> 8) * 0x1p-24f;
+        *reinterpret_cast<float2 *>(o + f32_off) = f;
+      }
+    } else if (n == ST) {
 #pragma unroll
       for (int h = 0; h < ST / 4; ++h) {
         const uint4 v = reinterpret_cast<const uint4 *>(src)[h];

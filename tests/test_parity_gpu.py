@@ -442,3 +442,31 @@ def test_roofline_probes_stay_below_the_lop3_rate():
         N.check(L.mickey_probe_clock(bps, 1024, ctypes.byref(x), ctypes.byref(mhz)))
         assert 40.0 < x.value <= 64.5, (bps, x.value)
         assert 500.0 < mhz.value < 2200.0, mhz.value
+
+
+@pytest.mark.parametrize("mode,depth", [("grid", 2), ("grid", 4), ("persistent", 2),
+                                        ("persistent", 4), ("persistent", 8),
+                                        ("persistent2", 4)])
+@pytest.mark.parametrize("n,n_bits", [(10 * 1024 + 7, 1024), (41 * 1024 - 3, 2048),
+                                      (3000, 768)])
+def test_output_tile_depths_match_direct_and_oracle(n, n_bits, mode, depth):
+    # rows staged `depth` tiles deep (the autotuner's output-tile axis) give
+    # the same bytes as direct row stores, and the oracle's on sampled rows
+    modes = {"grid": N.MODE_GRID, "persistent": N.MODE_PERSISTENT,
+             "persistent2": N.MODE_PERSISTENT2}
+    s = workloads.plain_scale(n)
+    L = N.lib()
+    st_d, st_s = _streams(s), _streams(s)
+    for layout in (N.LAYOUT_BYTES, N.LAYOUT_U32_F32):
+        N.check(L.mickey_set_config(st_d._h, layout, N.MODE_GRID, 4, 0))
+        N.check(L.mickey_set_config(st_s._h, layout, modes[mode], 4, depth))
+    a = st_d.generate(n_bits, "bytes").cpu().numpy()
+    b = st_s.generate(n_bits, "bytes").cpu().numpy()
+    c = st_d.generate(n_bits, "u32_f32").cpu().numpy()
+    d = st_s.generate(n_bits, "u32_f32").cpu().numpy()
+    st_s.sync()
+    assert np.array_equal(a, b) and np.array_equal(c, d)
+    rows = _sample_rows(n, 64, 9)
+    ref = _ref(s.subset(rows), 2 * n_bits)
+    assert np.array_equal(b[rows], ref[:, : n_bits // 8])
+    assert np.array_equal(d[0][rows].view(np.uint32), oracle.to_u32(ref[:, n_bits // 8:], n_bits))
