@@ -19,6 +19,13 @@
  *           cause in mickey_last_error() / mickey_last_error_message().
  *  Streams  work is enqueued on the handle's CUDA stream; calls return once
  *           it is enqueued.
+ *  Launch   with no more 32-group warp-groups than resident warps, one warp
+ *           per warp-group clocks the whole call; with more, a persistent
+ *           launch takes (warp-group, 1280-clock chunk) items from a queue,
+ *           each chunk continuing from the state its predecessor published
+ *           (a bounded wait: MICKEY_SPIN_LIMIT polls of about 256 ns, after
+ *           which grain_sync reports MICKEY_E_TIMEOUT).  MICKEY_GRAIN_QUEUE=1,
+ *           read when a handle is created, forces the queue.
  */
 #ifndef GRAIN_H
 #define GRAIN_H
@@ -54,6 +61,7 @@ MICKEY_API int grain_generate(grain_streams *s, uint64_t n_bits, void *out, int 
 MICKEY_API size_t grain_output_bytes(size_t n, uint64_t n_bits, int layout);
 
 MICKEY_API int grain_set_stream(grain_streams *s, void *cuda_stream);
+/* Wait for the handle's stream; MICKEY_E_TIMEOUT if a queue wait ran out. */
 MICKEY_API int grain_sync(grain_streams *s);
 /* Keystream bits generated so far (the same for every instance). */
 MICKEY_API uint64_t grain_position(const grain_streams *s);
@@ -65,6 +73,16 @@ MICKEY_API int grain_export_state(grain_streams *s, uint8_t *states);
  * an initialisation clock), as the kernels compute it.  Host-only. */
 MICKEY_API int grain_ops_per_clock(int init);
 MICKEY_API void grain_free(grain_streams *s);
+
+/* Measurement helper: the bare bitsliced Grain clock (blocks_per_sm 1..4
+ * blocks of 64 threads per SM, one 32-lane group per thread, bodies x 80
+ * clocks from an arbitrary state; store != 0 also writes each clock's
+ * keystream word to shared memory), synchronously on the current device.
+ * Outputs (each may be NULL): grain_ops_per_clock(0) ops per group-clock per
+ * SM per SM-cycle, and the SM clock seen (MHz) -- the ceiling of the
+ * keystream kernels' clock at that many warps per SM. */
+MICKEY_API int grain_probe_clock(int blocks_per_sm, int bodies, int store, double *ops_per_sm_clk,
+                                 double *sm_mhz);
 
 #ifdef __cplusplus
 }

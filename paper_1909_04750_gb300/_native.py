@@ -99,6 +99,7 @@ SIGNATURES = {
     "grain_export_state": (c_int, [c_void_p, c_void_p]),
     "grain_ops_per_clock": (c_int, [c_int]),
     "grain_free": (None, [c_void_p]),
+    "grain_probe_clock": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p]),
 }
 
 

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -35,110 +36,13 @@
 #include "../../include/grain.h"
 #include "../../include/mickey.h"
 #include "bitslice.cuh"
+#include "grain_clock.cuh"
 #include "internal.h"
 
 namespace mickey {
 namespace {
 
-constexpr int kG = 80;               // register length
-constexpr int kGrainThreads = 64;    // groups per block
-constexpr int kRing = 160;           // keystream words per thread in the ring
-
-__device__ __forceinline__ uint32_t xor3(uint32_t a, uint32_t b, uint32_t c) {
-  return lop3<0x96>(a, b, c);
-}
-__device__ __forceinline__ uint32_t and3(uint32_t a, uint32_t b, uint32_t c) {
-  return lop3<0x80>(a, b, c);
-}
-__device__ __forceinline__ uint32_t xand(uint32_t a, uint32_t b, uint32_t c) {
-  return lop3<0x78>(a, b, c);   // a ^ (b & c)
-}
-
-// One clock at rotation R (compile-time): returns z of the current state
-// and replaces slot R of both registers by the new bits.  The XOR sums are
-// balanced trees (at most five dependent steps to the new NFSR bit, four to
-// z), so that the instructions of one clock can issue back to back.
-template <int R, bool INIT>
-__device__ __forceinline__ uint32_t grain_clock(uint32_t (&s)[kG], uint32_t (&b)[kG]) {
-#define S(i) s[(R + (i)) % kG]
-#define B(i) b[(R + (i)) % kG]
-  // output: z = b1+b2+b4+b10+b31+b43+b56 + h(x0..x4),
-  // h = A + x2 B, A = x1+x4+x3(x0+x4), B = x3+x4(x1+x3)+x0(x1+x3+x4)
-  const uint32_t x0 = S(3), x1 = S(25), x2 = S(46), x3 = S(64), x4 = B(63);
-  const uint32_t t1 = xor3(B(1), B(2), B(4));
-  const uint32_t t2 = xor3(B(10), B(31), B(43));
-  const uint32_t u0 = xor3(x1, x4, B(56));
-  const uint32_t t = x0 ^ x4;
-  const uint32_t w = x1 ^ x3;
-  const uint32_t v = xor3(x1, x3, x4);
-  const uint32_t u = xor3(t1, t2, u0);                 // x1 + x4 + (b sum)
-  const uint32_t c = xand(x3, x4, w);                  // x3 + x4(x1 + x3)
-  const uint32_t a = xand(u, x3, t);                   // A + (b sum)
-  const uint32_t bb = xand(c, x0, v);                  // B
-  const uint32_t z = xand(a, x2, bb);                  // A + x2 B + (b sum)
-  // LFSR: s62+s51+s38+s23+s13+s0 (+ z while initialising)
-  const uint32_t la = xor3(S(62), S(51), S(38));
-  const uint32_t lb = xor3(S(23), S(13), S(0));
-  const uint32_t ns = INIT ? xor3(la, lb, z) : la ^ lb;
-  // NFSR: s0 + g(b), the 23 terms in a tree
-  const uint32_t p1 = B(63) & B(60);
-  const uint32_t p2 = B(37) & B(33);
-  const uint32_t p3 = B(15) & B(9);
-  const uint32_t q = B(60) & B(52);
-  const uint32_t r = B(52) & B(45);
-  const uint32_t p5 = and3(B(33), B(28), B(21));
-  const uint32_t p6 = and3(B(63), B(45), B(28));
-  const uint32_t l1 = xor3(B(62), B(60), B(52));
-  const uint32_t l2 = xor3(B(45), B(37), B(33));
-  const uint32_t l3 = xor3(B(28), B(21), B(14));
-  const uint32_t l4 = xor3(B(9), B(0), S(0));
-  const uint32_t m1 = xor3(l1, l2, l3);                 // the linear terms ...
-  const uint32_t m2 = xor3(l4, p1, p2);                 // ... s0, b63b60, b37b33
-  const uint32_t m3 = xand(p3, q, B(45));               // b15b9, b60b52b45
-  const uint32_t m4 = xand(p5, p6, B(9));               // b33b28b21, b63b45b28b9
-  const uint32_t t8 = and3(p1, B(21), B(15));           // b63b60b21b15
-  const uint32_t t9 = and3(p1, r, B(37));               // b63b60b52b45b37
-  const uint32_t t11 = and3(r, B(37), p5);              // b52b45b37b33b28b21
-  const uint32_t n1 = xor3(m1, m2, m3);
-  const uint32_t n2 = xand(m4, q, p2);                  // b60b52b37b33
-  const uint32_t n3 = xor3(t8, t9, t11);
-  const uint32_t n4 = xand(n2, p5, p3);                 // b33b28b21b15b9
-  uint32_t nb = xor3(n1, n4, n3);
-  if (INIT) nb ^= z;
-  S(0) = ns;   // slot R: the oldest bit becomes the newest
-  B(0) = nb;
-#undef S
-#undef B
-  return z;
-}
-
-// 80 clocks (one full rotation); keystream word of clock c to zb[c * kGrainThreads].
-template <bool INIT>
-__device__ __forceinline__ void grain_body(uint32_t (&s)[kG], uint32_t (&b)[kG], uint32_t *zb) {
-  static_for<0, kG>([&](auto rc) {
-    constexpr int R = decltype(rc)::value;
-    const uint32_t z = grain_clock<R, INIT>(s, b);
-    if constexpr (!INIT) zb[R * kGrainThreads] = z;
-  });
-}
-
-// One clock with the registers physically shifted (rotation stays 0): the
-// tail of a call, fewer than 80 clocks.
-__device__ __forceinline__ uint32_t grain_clock_shift(uint32_t (&s)[kG], uint32_t (&b)[kG]) {
-  const uint32_t s0 = s[0], b0 = b[0];
-  const uint32_t z = grain_clock<0, false>(s, b);   // writes the new bits to slot 0
-  const uint32_t ns = s[0], nb = b[0];
-  s[0] = s0;
-  b[0] = b0;
-  static_for<0, kG - 1>([&](auto ic) {
-    constexpr int i = decltype(ic)::value;
-    s[i] = s[i + 1];
-    b[i] = b[i + 1];
-  });
-  s[kG - 1] = ns;
-  b[kG - 1] = nb;
-  return z;
-}
+using namespace grainc;
 
 struct GrainArgs {
   uint32_t *state;      // 160 x Gpad words: s0..s79 then b0..b79
@@ -147,6 +51,21 @@ struct GrainArgs {
   uint64_t n_bits;
   void *out;
   uint32_t last_mask;   // valid lanes of the last group
+};
+
+// Clocks per queue item: a multiple of the ring (160) and of the row staging
+// (8 tiles = 256 clocks), so that every item starts on a fresh body, tile and
+// staged block.
+constexpr uint64_t kChunk = 1280;
+
+struct GrainQueue {
+  uint32_t *counter;    // items taken, zero at launch
+  uint32_t *flags;      // per warp-group: chunks finished, zero at launch
+  uint32_t W;           // warp-groups
+  uint64_t chunk;       // clocks per item
+  uint64_t n_chunks;
+  uint32_t spin_limit;  // polls of ~256 ns before a wait gives up
+  int *err;
 };
 
 // Row staging of the bytes layout: the transposed words of 8 consecutive
@@ -164,6 +83,7 @@ __device__ __forceinline__ void grain_emit(uint32_t *zb, uint32_t *rb, const Gra
                                            uint32_t g, uint64_t k, int nb, uint32_t mask) {
   constexpr int T = kGrainThreads;
   const uint64_t t0 = k << 5;
+  if (mask == 0) return;                   // a lane past the last group: nothing to store
   if constexpr (LAYOUT == MICKEY_LAYOUT_BITSLICED_U32) {
     uint32_t *o = static_cast<uint32_t *>(a.out) + size_t(g) * a.n_bits + t0;
     if (nb == 32 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
@@ -237,51 +157,114 @@ __device__ __forceinline__ void grain_emit(uint32_t *zb, uint32_t *rb, const Gra
   }
 }
 
+// Clocks [t_a, t_b) of the call for group g (t_a a multiple of kChunk, so
+// that its bodies, ring slots, tiles and staged blocks line up), from and back
+// to the state in HBM; `live` is false for the lanes of a warp past the last
+// group, which clock a copy of group 0's state and store nothing.
 template <int LAYOUT>
-__global__ void __launch_bounds__(kGrainThreads) grain_keystream_kernel(GrainArgs a) {
-  // shared memory: the keystream ring (kRing words per thread, [word][thread])
-  // and, for the bytes layout, the row staging ([lane][thread][8])
-  extern __shared__ __align__(16) uint32_t ring[];
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.G) return;
+__device__ __forceinline__ void grain_piece(const GrainArgs &a, uint32_t g, bool live,
+                                            uint64_t t_a, uint64_t t_b, uint32_t *zb,
+                                            uint32_t *rb) {
   const size_t P = a.Gpad;
+  const uint32_t gs = live ? g : 0;
   uint32_t s[kG], b[kG];
 #pragma unroll
   for (int i = 0; i < kG; ++i) {
-    s[i] = a.state[size_t(i) * P + g];
-    b[i] = a.state[size_t(kG + i) * P + g];
+    s[i] = a.state[size_t(i) * P + gs];
+    b[i] = a.state[size_t(kG + i) * P + gs];
   }
-  const uint32_t mask = g == a.G - 1 ? a.last_mask : ~0u;
-  uint32_t *zb = ring + threadIdx.x;
-  uint32_t *rb = ring + kRing * kGrainThreads + threadIdx.x * kStage;
-  const uint64_t full = a.n_bits / kG;       // whole bodies of 80 clocks
-  uint64_t emitted = 0;                      // tiles emitted so far
+  const uint32_t mask = !live ? 0u : g == a.G - 1 ? a.last_mask : ~0u;
+  const uint64_t n = t_b - t_a;
+  const uint64_t full = n / kG;             // whole bodies of 80 clocks
+  uint64_t emitted = 0;                     // tiles of this piece emitted so far
 #pragma unroll 1
   for (uint64_t j = 0; j < full; ++j) {
     grain_body<false>(s, b, zb + (j & 1) * kG * kGrainThreads);
     const uint64_t done = (j + 1) * kG;
 #pragma unroll 1
     for (; (emitted + 1) * 32 <= done; ++emitted)
-      grain_emit<LAYOUT>(zb + ((emitted * 32) % kRing) * kGrainThreads, rb, a, g, emitted, 32,
-                         mask);
+      grain_emit<LAYOUT>(zb + ((emitted * 32) % kRing) * kGrainThreads, rb, a, g,
+                         (t_a >> 5) + emitted, 32, mask);
   }
-  const int rem = int(a.n_bits - full * kG);
+  const int rem = int(n - full * kG);
   if (rem) {
     uint32_t *zt = zb + (full & 1) * kG * kGrainThreads;
 #pragma unroll 1
     for (int c = 0; c < rem; ++c) zt[c * kGrainThreads] = grain_clock_shift(s, b);
   }
 #pragma unroll 1
-  for (; emitted * 32 < a.n_bits; ++emitted) {
-    const int nb = int(min(uint64_t(32), a.n_bits - emitted * 32));
+  for (; emitted * 32 < n; ++emitted) {
+    const int nb = int(min(uint64_t(32), n - emitted * 32));
     uint32_t *zt = zb + ((emitted * 32) % kRing) * kGrainThreads;
     for (int c = nb; c < 32; ++c) zt[c * kGrainThreads] = 0u;   // past the call's last clock
-    grain_emit<LAYOUT>(zt, rb, a, g, emitted, nb, mask);
+    grain_emit<LAYOUT>(zt, rb, a, g, (t_a >> 5) + emitted, nb, mask);
   }
+  if (live) {
 #pragma unroll
-  for (int i = 0; i < kG; ++i) {
-    a.state[size_t(i) * P + g] = s[i];
-    a.state[size_t(kG + i) * P + g] = b[i];
+    for (int i = 0; i < kG; ++i) {
+      a.state[size_t(i) * P + g] = s[i];
+      a.state[size_t(kG + i) * P + g] = b[i];
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t grain_load_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void grain_store_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Persistent launch (every block resident; used when there are more
+// warp-groups than resident warps): warps take items from a queue,
+// item i = chunk i / W of warp-group i % W (W warp-groups of 32 groups,
+// chunks of kChunk clocks), so that all first chunks come first.  Chunk k of
+// a warp-group starts from the state its chunk k - 1 published: the warp
+// waits (bounded) until the warp-group's flag reaches k.  That item was taken
+// from the queue earlier by a warp that is running, so the wait ends; if it
+// runs out the error flag is raised and the item is skipped (the call's
+// output and state are then undefined, and grain_sync reports it).  Every SM
+// sub-partition keeps its full share of warps until the queue runs dry.
+template <int LAYOUT>
+__global__ void __launch_bounds__(kGrainThreads) grain_keystream_kernel(GrainArgs a, GrainQueue q) {
+  // shared memory: the keystream ring (kRing words per thread, [word][thread])
+  // and, for the bytes layout, the row staging ([lane][thread][8])
+  extern __shared__ __align__(16) uint32_t ring[];
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t *zb = ring + threadIdx.x;
+  uint32_t *rb = ring + kRing * kGrainThreads + threadIdx.x * kStage;
+  const uint64_t items = uint64_t(q.W) * q.n_chunks;
+#pragma unroll 1
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(q.counter, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= items) break;
+    const uint32_t k = item / q.W, w = item % q.W;
+    if (k > 0) {   // every lane acquires the predecessor's published state
+      uint32_t it = 0;
+      bool ok = true;
+      while (grain_load_acquire(q.flags + w) < k) {
+        if (++it > q.spin_limit) {
+          ok = false;
+          break;
+        }
+        __nanosleep(256);
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(q.err, kErrTimeout);
+        continue;
+      }
+    }
+    const uint32_t g = w * 32 + lane;
+    const uint64_t t_a = uint64_t(k) * q.chunk;
+    const uint64_t t_b = min(a.n_bits, t_a + q.chunk);
+    grain_piece<LAYOUT>(a, g, g < a.G, t_a, t_b, zb, rb);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) grain_store_release(q.flags + w, k + 1);
   }
 }
 
@@ -299,19 +282,24 @@ constexpr int kInitT = 64;                   // groups per block
 constexpr int kKeyWords = 81;                // 80 words of 32 keys + a spare (odd stride)
 constexpr int kIvWords = 65;                 // 64 words of 32 IVs + a spare
 
-// Copy `bytes` bytes of src into rows of row_bytes bytes, stride_words apart.
+// Copy `bytes` bytes of src into rows of row_bytes bytes, stride_words apart:
+// 4-byte cp.async copies (all in flight at once; the caller waits) when src
+// is 4-byte aligned, byte loads otherwise and for a last partial word.
 __device__ __forceinline__ void stage(const uint8_t *src, uint64_t bytes, uint32_t *dst,
                                       int row_bytes, int stride_words) {
   const int row_words = row_bytes / 4;
+  const bool aligned = (reinterpret_cast<uintptr_t>(src) & 3u) == 0;
   for (uint64_t w = threadIdx.x; w * 4 < bytes; w += kInitT) {
-    uint32_t v;
-    if ((reinterpret_cast<uintptr_t>(src) & 3u) == 0 && w * 4 + 4 <= bytes) {
-      v = reinterpret_cast<const uint32_t *>(src)[w];
+    uint32_t *d = dst + (w / row_words) * stride_words + w % row_words;
+    if (aligned && w * 4 + 4 <= bytes) {
+      const uint32_t da = uint32_t(__cvta_generic_to_shared(d));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(da),
+                   "l"(reinterpret_cast<const uint32_t *>(src) + w) : "memory");
     } else {
-      v = 0;
+      uint32_t v = 0;
       for (int k = 0; k < 4 && w * 4 + k < bytes; ++k) v |= uint32_t(src[w * 4 + k]) << (8 * k);
+      *d = v;
     }
-    dst[(w / row_words) * stride_words + w % row_words] = v;
   }
 }
 
@@ -329,6 +317,7 @@ __global__ void __launch_bounds__(kInitT) grain_init_kernel(GrainInitArgs a) {
   const uint64_t count = min(uint64_t(32) * kInitT, a.n - first);
   stage(a.keys + first * 10, count * 10, ks, 320, kKeyWords);
   stage(a.ivs + first * 8, count * 8, vs, 256, kIvWords);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= a.G) return;
@@ -370,8 +359,10 @@ __global__ void __launch_bounds__(kInitT) grain_init_kernel(GrainInitArgs a) {
   });
 #pragma unroll
   for (int i = 64; i < kG; ++i) s[i] = ~0u;    // s64..s79 = 1
-  grain_body<true>(s, b, nullptr);             // 160 clocks, z fed back
-  grain_body<true>(s, b, nullptr);
+  // 160 clocks with z fed back: one 80-clock rotation, run twice (the
+  // mapping of slots to register bits is back at the start after 80)
+#pragma unroll 1
+  for (int rep = 0; rep < 2; ++rep) grain_body<true>(s, b, nullptr);
   const size_t P = a.Gpad;
 #pragma unroll
   for (int i = 0; i < kG; ++i) {
@@ -380,16 +371,55 @@ __global__ void __launch_bounds__(kInitT) grain_init_kernel(GrainInitArgs a) {
   }
 }
 
+// One thread per group for the whole call (used when every warp-group fits
+// in the resident warps at once, so that the queue would add waits and no
+// parallelism: a warp-group's chunks cannot overlap).
 template <int LAYOUT>
-cudaError_t launch_grain_layout(const GrainArgs &a, cudaStream_t st) {
+__global__ void __launch_bounds__(kGrainThreads) grain_grid_kernel(GrainArgs a) {
+  extern __shared__ __align__(16) uint32_t ring[];
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.G) return;
+  grain_piece<LAYOUT>(a, g, true, 0, a.n_bits, ring + threadIdx.x,
+                      ring + kRing * kGrainThreads + threadIdx.x * kStage);
+}
+
+template <int LAYOUT>
+cudaError_t launch_grain_layout(const GrainArgs &a, const GrainQueue &q, int sm_count,
+                                bool force_queue, cudaStream_t st) {
   const size_t smem = size_t(kRing) * kGrainThreads * 4 +
                       (LAYOUT == MICKEY_LAYOUT_BYTES ? size_t(32) * kGrainThreads * kStage * 4 : 0);
   cudaError_t e = cudaFuncSetAttribute(grain_keystream_kernel<LAYOUT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  grain_keystream_kernel<LAYOUT><<<(a.G + kGrainThreads - 1) / kGrainThreads, kGrainThreads, smem,
-                                   st>>>(a);
-  return cudaGetLastError();
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grain_keystream_kernel<LAYOUT>,
+                                                    kGrainThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t slots = uint64_t(per_sm) * sm_count * (kGrainThreads / 32);
+  if (q.W <= slots && !force_queue) {   // every warp-group gets a warp of its own
+    e = cudaFuncSetAttribute(grain_grid_kernel<LAYOUT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    grain_grid_kernel<LAYOUT><<<(a.G + kGrainThreads - 1) / kGrainThreads, kGrainThreads, smem,
+                                st>>>(a);
+    return cudaGetLastError();
+  }
+  // every block resident (the waits need it); no more warps than items
+  const uint64_t items = uint64_t(q.W) * q.n_chunks;
+  const uint64_t want = (items + kGrainThreads / 32 - 1) / (kGrainThreads / 32);
+  const uint32_t blocks = uint32_t(std::min<uint64_t>(uint64_t(per_sm) * sm_count, want));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kGrainThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, grain_keystream_kernel<LAYOUT>, a, q);
 }
 
 // Logic ops per clock per 32-lane group, as written above (keystream clock
@@ -407,8 +437,13 @@ struct grain_streams {
   uint32_t G = 0, Gpad = 0;
   uint32_t *d_state = nullptr;
   uint8_t *d_inputs = nullptr;   // host inputs staged: keys (10n), ivs (8n)
+  uint32_t *d_queue = nullptr;   // item counter, then one flag per warp-group
+  int *d_err = nullptr;
   cudaStream_t stream = nullptr;
   uint64_t pos = 0;
+  int sm_count = 0;
+  uint32_t spin_limit = 1u << 24;
+  bool force_queue = false;      // MICKEY_GRAIN_QUEUE=1: always the queue-fed launch
 };
 
 namespace {
@@ -420,6 +455,8 @@ void grain_release(grain_streams *s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   cudaFree(s->d_state);
   cudaFree(s->d_inputs);
+  cudaFree(s->d_queue);
+  cudaFree(s->d_err);
   delete s;
 }
 
@@ -450,7 +487,19 @@ MICKEY_API grain_streams *grain_init_streams(const void *keys, const void *ivs, 
   s->Gpad = (s->G + 31u) & ~31u;
   s->stream = static_cast<cudaStream_t>(cuda_stream);
   const uint8_t *dk = static_cast<const uint8_t *>(keys), *dv = static_cast<const uint8_t *>(ivs);
-  bool ok = cudaMalloc(&s->d_state, size_t(2 * kG) * s->Gpad * 4) == cudaSuccess;
+  int dev = 0;
+  bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev) ==
+                cudaSuccess &&
+            cudaMalloc(&s->d_state, size_t(2 * kG) * s->Gpad * 4) == cudaSuccess &&
+            cudaMalloc(&s->d_queue, (1 + size_t(s->Gpad / 32)) * 4) == cudaSuccess &&
+            cudaMalloc(&s->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream) == cudaSuccess;
+  if (const char *v = getenv("MICKEY_SPIN_LIMIT")) {
+    const long long l = atoll(v);
+    if (l > 0 && l < (1ll << 31)) s->spin_limit = uint32_t(l);
+  }
+  if (const char *v = getenv("MICKEY_GRAIN_QUEUE")) s->force_queue = atoi(v) != 0;
   if (ok && mem == MICKEY_MEM_HOST) {
     ok = cudaMalloc(&s->d_inputs, n * 18) == cudaSuccess &&
          cudaMemcpyAsync(s->d_inputs, keys, n * 10, cudaMemcpyHostToDevice, s->stream) ==
@@ -506,9 +555,16 @@ MICKEY_API int grain_generate(grain_streams *s, uint64_t n_bits, void *out, int 
     return grain_fail(MICKEY_E_ARG, "bitsliced output must be 4-byte aligned");
   const uint32_t tail = uint32_t(s->n & 31u);
   GrainArgs a{s->d_state, s->G, s->Gpad, s->n, n_bits, out, tail ? (1u << tail) - 1u : ~0u};
-  const cudaError_t e = layout == MICKEY_LAYOUT_BYTES
-                            ? launch_grain_layout<MICKEY_LAYOUT_BYTES>(a, s->stream)
-                            : launch_grain_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, s->stream);
+  const uint32_t W = (s->G + 31) / 32;
+  GrainQueue q{s->d_queue, s->d_queue + 1, W, kChunk, (n_bits + kChunk - 1) / kChunk,
+               s->spin_limit, s->d_err};
+  if (cudaMemsetAsync(s->d_queue, 0, (1 + size_t(W)) * 4, s->stream) != cudaSuccess)
+    return grain_fail(MICKEY_E_CUDA, "queue reset");
+  const cudaError_t e =
+      layout == MICKEY_LAYOUT_BYTES
+          ? launch_grain_layout<MICKEY_LAYOUT_BYTES>(a, q, s->sm_count, s->force_queue, s->stream)
+          : launch_grain_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, q, s->sm_count, s->force_queue,
+                                                             s->stream);
   if (e != cudaSuccess) return grain_fail(MICKEY_E_CUDA, "grain keystream launch");
   s->pos += n_bits;
   return set_error(MICKEY_OK, "");
@@ -528,6 +584,13 @@ MICKEY_API int grain_sync(grain_streams *s) {
   if (!s) return grain_fail(MICKEY_E_ARG, "NULL handle");
   if (cudaStreamSynchronize(s->stream) != cudaSuccess)
     return grain_fail(MICKEY_E_CUDA, "cudaStreamSynchronize");
+  int flag = 0;
+  if (cudaMemcpy(&flag, s->d_err, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return grain_fail(MICKEY_E_CUDA, "error flag copy");
+  if (flag) {
+    cudaMemset(s->d_err, 0, sizeof(int));
+    return grain_fail(MICKEY_E_TIMEOUT, "a device-side wait timed out");
+  }
   return set_error(MICKEY_OK, "");
 }
 

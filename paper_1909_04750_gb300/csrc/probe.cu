@@ -10,8 +10,10 @@
 
 #include <vector>
 
+#include "../../include/grain.h"
 #include "../../include/mickey.h"
 #include "bitslice.cuh"
+#include "grain_clock.cuh"
 
 namespace {
 
@@ -78,7 +80,100 @@ __global__ void __launch_bounds__(128, 1)
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// The bare Grain clock: 64 threads per block, one 32-lane group per thread,
+// `bodies` x 80 clocks from an arbitrary state; STORE writes each clock's
+// keystream word to shared memory (as the keystream kernel's ring does),
+// otherwise the words are folded into an accumulator.
+template <bool STORE>
+__global__ void __launch_bounds__(mickey::grainc::kGrainThreads)
+    grain_clock_probe_kernel(uint32_t *state, int bodies, long long *cycles, uint32_t *sink) {
+  using namespace mickey::grainc;
+  __shared__ uint32_t zb[kG * kGrainThreads];
+  const uint32_t G = gridDim.x * blockDim.x;
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t s[kG], b[kG];
+#pragma unroll
+  for (int i = 0; i < kG; ++i) {
+    s[i] = state[size_t(i) * G + g];
+    b[i] = state[size_t(kG + i) * G + g];
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  uint32_t acc = 0;
+#pragma unroll 1
+  for (int k = 0; k < bodies; ++k) {
+    if constexpr (STORE) {
+      grain_body<false>(s, b, zb + threadIdx.x);
+    } else {
+      mickey::static_for<0, kG>([&](auto rc) {
+        constexpr int R = decltype(rc)::value;
+        acc ^= grain_clock<R, false>(s, b);
+      });
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  if constexpr (STORE) acc = zb[threadIdx.x];
+#pragma unroll
+  for (int i = 0; i < kG; ++i) acc ^= s[i] ^ b[i];
+  sink[g] = acc;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace
+
+extern "C" MICKEY_API int grain_probe_clock(int blocks_per_sm, int bodies, int store,
+                                            double *ops_per_sm_clk, double *sm_mhz) {
+  using namespace mickey::grainc;
+  if (blocks_per_sm < 1 || blocks_per_sm > 4 || bodies < 1) return MICKEY_E_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MICKEY_E_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MICKEY_E_CUDA;
+  const int blocks = sms * blocks_per_sm;
+  const size_t G = size_t(blocks) * kGrainThreads;
+  uint32_t *state = nullptr, *sink = nullptr;
+  long long *cyc = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = MICKEY_OK;
+  if (cudaMalloc(&state, G * 2 * kG * 4) != cudaSuccess || cudaMalloc(&sink, G * 4) != cudaSuccess ||
+      cudaMalloc(&cyc, blocks * sizeof(long long)) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = MICKEY_E_CUDA;
+  } else {
+    cudaMemset(state, 0x5a, G * 2 * kG * 4);   // any state that is not all zeros or ones
+    auto launch = [&](int n) {
+      if (store)
+        grain_clock_probe_kernel<true><<<blocks, kGrainThreads>>>(state, n, cyc, sink);
+      else
+        grain_clock_probe_kernel<false><<<blocks, kGrainThreads>>>(state, n, cyc, sink);
+    };
+    launch(2);   // warm-up
+    cudaEventRecord(e0);
+    launch(bodies);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = MICKEY_E_CUDA;
+    } else {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      std::vector<long long> h(blocks);
+      cudaMemcpy(h.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+      long long mx = 0;
+      for (long long c : h) mx = c > mx ? c : mx;
+      const double ops_sm =
+          double(kGrainThreads) * blocks_per_sm * double(bodies) * kG * grain_ops_per_clock(0);
+      if (ops_per_sm_clk) *ops_per_sm_clk = ops_sm / double(mx);
+      if (sm_mhz) *sm_mhz = double(mx) / (ms * 1e3);
+    }
+  }
+  cudaFree(state);
+  cudaFree(sink);
+  cudaFree(cyc);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}
 
 extern "C" MICKEY_API int mickey_probe_clock(int blocks_per_sm, int clocks, double *ops_per_sm_clk,
                                              double *sm_mhz) {

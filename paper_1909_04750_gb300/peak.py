@@ -78,6 +78,22 @@ def main():
         print("bare clock, %d warp(s) per SM sub-partition: %.1f algorithmic ops/SM/clk "
               "= %.3f of %.1f, at %.0f MHz" % (bps, a.value, a.value / m["lop3_per_sm_clk"],
                                                m["lop3_per_sm_clk"], b.value), flush=True)
+    # the bare Grain clock at 1 and 2 warps per SM sub-partition
+    for bps in (2, 4):
+        for store in (False, True):
+            r, mhz = grain_clock(bps, store)
+            print("bare Grain clock, %d warp(s) per SM sub-partition%s: %.1f ops/SM/clk = %.3f "
+                  "of %.1f, at %.0f MHz" % (bps // 2, ", keystream words to shared memory"
+                                            if store else "", r, r / m["lop3_per_sm_clk"],
+                                            m["lop3_per_sm_clk"], mhz), flush=True)
+
+
+def grain_clock(blocks_per_sm: int, store: bool, bodies: int = 200):
+    """Bare Grain clock: (ops per SM per SM-cycle, SM MHz)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    N.check(N.lib().grain_probe_clock(blocks_per_sm, bodies, 1 if store else 0, ctypes.byref(a),
+                                      ctypes.byref(b)))
+    return a.value, b.value
 
 
 if __name__ == "__main__":

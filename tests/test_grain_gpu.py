@@ -29,6 +29,24 @@ def _gs(s):
     return GrainStreams(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda())
 
 
+@pytest.mark.parametrize("n,n_bits", [(1000, 3000), (3 * 1024 + 17, 2560), (2100, 1281),
+                                      (64, 6000)])
+def test_queue_fed_launch_every_instance(monkeypatch, n, n_bits):
+    # the persistent launch with (warp-group, chunk) items, forced for a few
+    # warp-groups: every chunk after the first waits for its predecessor
+    monkeypatch.setenv("MICKEY_GRAIN_QUEUE", "1")
+    s = workloads.grain_streams(n, seed=16)
+    ref = og.batch_bytes(s.keys, s.ivs, n_bits, threads=THREADS)
+    st = _gs(s)
+    got = st.generate(n_bits, "bytes").cpu().numpy()
+    st.sync()
+    assert np.array_equal(got, ref)
+    st2 = _gs(s)
+    words = st2.generate(n_bits, "bitsliced").cpu().numpy().view(np.uint32)
+    st2.sync()
+    assert np.array_equal(words, og.to_bitsliced(ref, n_bits))
+
+
 def test_known_answer_vectors_on_the_gpu():
     from paper_1909_04750_gb300.grain import GrainStreams
     rows = [l.split() for l in open(os.path.join(GOLDEN, "grain_kat.txt"))
@@ -43,7 +61,8 @@ def test_known_answer_vectors_on_the_gpu():
 
 
 @pytest.mark.parametrize("n,n_bits", [(32, 4096), (70, 1000), (33, 161), (5, 1), (64, 7),
-                                      (96, 80), (40, 159), (31, 320)])
+                                      (96, 80), (40, 159), (31, 320), (1000, 3000),
+                                      (3 * 1024 + 17, 2560), (2100, 1281)])
 def test_every_instance_both_layouts(n, n_bits):
     s = workloads.grain_streams(n, seed=11)
     ref = og.batch_bytes(s.keys, s.ivs, n_bits, threads=THREADS)
