@@ -154,6 +154,8 @@ MICKEY_API size_t mickey_output_bytes(size_t n, uint64_t n_bits, int layout);
  *                 (4-byte aligned; 16 for vector stores), C_g the longest
  *                 n_bits of its lanes; bit l of word t is z_t of instance
  *                 32g + l while t < n_bits[32g + l], else 0.
+ * Equal lengths at the packed offsets are mickey_generate's layout and run
+ * as its keystream launch.
  * Asynchronous on the handle's stream.  Errors (nothing is launched and no
  * position moves): MICKEY_E_ARG (NULL pointer, a length above 2^34, a
  * misaligned 32-bit output), MICKEY_E_LAYOUT (MICKEY_LAYOUT_U32_F32, or a
@@ -164,7 +166,8 @@ MICKEY_API int mickey_generate_ragged(mickey_streams *s, const uint64_t *n_bits,
                                       const uint64_t *out_offsets, int layout);
 
 /* Size in bytes of the packed output of mickey_generate_ragged for these n
- * lengths; 0 for a layout it does not take. */
+ * lengths; 0 for a layout it does not take, a u32 length not a multiple of
+ * 32, or a length above 2^34 (the per-call limit). */
 MICKEY_API size_t mickey_ragged_output_bytes(size_t n, const uint64_t *n_bits, int layout);
 
 /* As mickey_generate into a HOST buffer (pinned memory gives full copy

@@ -47,34 +47,33 @@ __host__ __device__ constexpr uint32_t s_lut(bool c0, bool c1) {
   return (0xF0u ^ ((0xCCu ^ (c0 ? 0xFFu : 0u)) & (0xAAu ^ (c1 ? 0xFFu : 0u)))) & 0xFFu;
 }
 
-// One bitsliced CLOCK_KG for 32 lanes.
-//   MIX   mixing mode (key/IV loading and preclocks): the R input takes
-//         in ^ s50, both feedbacks take `in` (bit l = input bit of lane l).
-//   MASK  lanes whose bit in `act` is 0 keep their state.  Only used while
-//         lanes with shorter IVs have not started their IV clocks: such a
-//         lane's state is all zero and its input bits are zero, and a clock
-//         of the zero state with zero input changes nothing except the S
-//         positions i where COMP0_i = COMP1_i = 1 (s^_i gets c0 & c1 = 1),
-//         so AND-ing `act` into the non-linear term of exactly those
-//         positions keeps inactive lanes at zero.
-// Both registers are clocked from the old state (control bits
-// CONTROL_BIT_R = s34 ^ r67, CONTROL_BIT_S = s67 ^ r33).  Instruction
-// count: one per bit of R and of S, one more where feedback enters, and
-// CBR, FB&~CBS, FB&CBS (CBS folded into the last two).
-template <bool MIX, bool MASK>
-__device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
-                                         uint32_t (&s)[kReg], uint32_t in,
-                                         uint32_t act) {
-  const uint32_t cbr = s[34] ^ r[67];
-  uint32_t fbr = r[99];
-  uint32_t fbs = s[99];
-  if constexpr (MIX) {
-    fbr = lop3<0x96>(fbr, in, s[50]);
-    fbs = fbs ^ in;
-  }
-  const uint32_t f0 = lop3<0x90>(fbs, s[67], r[33]);   // fbs & ~(s67 ^ r33)
-  const uint32_t f1 = lop3<0x60>(fbs, s[67], r[33]);   // fbs &  (s67 ^ r33)
+// The values every bit update of a clock reads besides its neighbours:
+// CONTROL_BIT_R, the R and S feedback bits, and FB & ~CBS, FB & CBS.
+struct KgFeed {
+  uint32_t cbr, fbr, fbs, f0, f1;
+};
 
+template <bool MIX>
+__device__ __forceinline__ KgFeed kg_feed(const uint32_t (&r)[kReg], const uint32_t (&s)[kReg],
+                                          uint32_t in) {
+  KgFeed f;
+  f.cbr = s[34] ^ r[67];
+  f.fbr = r[99];
+  f.fbs = s[99];
+  if constexpr (MIX) {
+    f.fbr = lop3<0x96>(f.fbr, in, s[50]);
+    f.fbs = f.fbs ^ in;
+  }
+  f.f0 = lop3<0x90>(f.fbs, s[67], r[33]);   // fbs & ~(s67 ^ r33)
+  f.f1 = lop3<0x60>(f.fbs, s[67], r[33]);   // fbs &  (s67 ^ r33)
+  return f;
+}
+
+// The bit updates of one clock from its feed values (clock_kg below).
+template <bool MASK>
+__device__ __forceinline__ void clock_kg_from(uint32_t (&r)[kReg], uint32_t (&s)[kReg],
+                                              const KgFeed &fd, uint32_t act) {
+  const uint32_t cbr = fd.cbr, fbr = fd.fbr, fbs = fd.fbs, f0 = fd.f0, f1 = fd.f1;
   uint32_t nr[kReg], ns[kReg];
   // CLOCK_R: r'_i = r_{i-1} ^ (cbr & r_i) ^ (i in RTAPS ? fb : 0), r_{-1} = 0
   nr[0] = lop3<0x6A>(cbr, r[0], fbr);                  // (cbr & r0) ^ fb
@@ -104,6 +103,27 @@ __device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
     r[i] = nr[i];
     s[i] = ns[i];
   });
+}
+
+// One bitsliced CLOCK_KG for 32 lanes.
+//   MIX   mixing mode (key/IV loading and preclocks): the R input takes
+//         in ^ s50, both feedbacks take `in` (bit l = input bit of lane l).
+//   MASK  lanes whose bit in `act` is 0 keep their state.  Only used while
+//         lanes with shorter IVs have not started their IV clocks: such a
+//         lane's state is all zero and its input bits are zero, and a clock
+//         of the zero state with zero input changes nothing except the S
+//         positions i where COMP0_i = COMP1_i = 1 (s^_i gets c0 & c1 = 1),
+//         so AND-ing `act` into the non-linear term of exactly those
+//         positions keeps inactive lanes at zero.
+// Both registers are clocked from the old state (control bits
+// CONTROL_BIT_R = s34 ^ r67, CONTROL_BIT_S = s67 ^ r33).  Instruction
+// count: one per bit of R and of S, one more where feedback enters, and
+// CBR, FB&~CBS, FB&CBS (CBS folded into the last two).
+template <bool MIX, bool MASK>
+__device__ __forceinline__ void clock_kg(uint32_t (&r)[kReg],
+                                         uint32_t (&s)[kReg], uint32_t in,
+                                         uint32_t act) {
+  clock_kg_from<MASK>(r, s, kg_feed<MIX>(r, s, in), act);
 }
 
 // In-register transpose of a 32 x 32 bit matrix.  Row k is a[k]; column c

@@ -46,10 +46,15 @@ struct mickey_streams {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
   // mickey_generate_ragged: device copies of the per-stream lengths and
-  // output offsets, and the event after the last launch that reads them
+  // output offsets, and the event after the last launch that reads them;
+  // two pinned host buffers they are copied from, each with the event after
+  // its last copy
   uint64_t *d_ragged = nullptr;
   size_t ragged_words = 0;
   cudaEvent_t ev_ragged = nullptr;
+  uint64_t *h_ragged[2] = {nullptr, nullptr};
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr};
+  int ragged_flip = 0;
 };
 
 namespace {
@@ -136,6 +141,10 @@ void release(mickey_streams *s) {
   cudaFree(s->d_flags);
   cudaFree(s->d_ragged);
   if (s->ev_ragged) cudaEventDestroy(s->ev_ragged);
+  for (int k = 0; k < 2; ++k) {
+    if (s->h_ragged[k]) cudaFreeHost(s->h_ragged[k]);
+    if (s->ev_h2d[k]) cudaEventDestroy(s->ev_h2d[k]);
+  }
   delete s;
 }
 
@@ -315,6 +324,23 @@ uint64_t ragged_packed(size_t n, const uint64_t *n_bits, int layout, uint64_t *o
   return off;
 }
 
+// True when every stream asks for the same number of bits and the offsets
+// (NULL = packed) are the packed ones: row i at i * row bytes, group g's
+// words at g * 4 * n_bits.
+bool equal_packed(size_t n, const uint64_t *n_bits, const uint64_t *offs, int layout) {
+  const uint64_t b = n_bits[0];
+  for (size_t i = 1; i < n; ++i)
+    if (n_bits[i] != b) return false;
+  if (b == 0 || !offs) return b != 0;
+  const size_t n_off = layout == MICKEY_LAYOUT_BITSLICED_U32 ? (n + 31) / 32 : n;
+  const uint64_t step = layout == MICKEY_LAYOUT_BITSLICED_U32 ? 4 * b
+                        : layout == MICKEY_LAYOUT_U32         ? b / 8
+                                                              : (b + 7) / 8;
+  for (size_t k = 0; k < n_off; ++k)
+    if (offs[k] != k * step) return false;
+  return true;
+}
+
 }  // namespace
 
 namespace mickey {
@@ -418,41 +444,68 @@ int mickey_generate_ragged(mickey_streams *s, const uint64_t *n_bits, void *out,
       return fail(MICKEY_E_LAYOUT, "the u32 layout needs n_bits[%zu] %% 32 == 0", i);
     any |= n_bits[i];
   }
-  std::vector<uint64_t> h(n + n_off);
-  std::copy(n_bits, n_bits + n, h.begin());
-  uint64_t *offs = h.data() + n;
-  if (out_offsets)
-    std::copy(out_offsets, out_offsets + n_off, offs);
-  else
-    ragged_packed(n, n_bits, layout, offs);
+  // 32-bit layouts: every output that receives words starts 4-byte aligned.
+  // Packed offsets are multiples of 4 there, so only the base can be off.
   const uintptr_t base = reinterpret_cast<uintptr_t>(out);
-  if (layout != MICKEY_LAYOUT_BYTES) {
-    for (size_t k = 0; k < n_off; ++k) {
-      uint64_t c = layout == MICKEY_LAYOUT_U32 ? n_bits[k] : 0;
-      if (layout == MICKEY_LAYOUT_BITSLICED_U32)
+  if (layout != MICKEY_LAYOUT_BYTES && any) {
+    for (size_t k = 0; k < (out_offsets ? n_off : 1); ++k) {
+      if ((base + (out_offsets ? out_offsets[k] : 0)) % 4 == 0) continue;
+      uint64_t c = 0;   // the words this output receives (none: no constraint)
+      if (!out_offsets) c = any;
+      else if (layout == MICKEY_LAYOUT_U32) c = n_bits[k];
+      else
         for (size_t i = 32 * k; i < n && i < 32 * k + 32; ++i) c = std::max(c, n_bits[i]);
-      if (c && (base + offs[k]) % 4)
+      if (c)
         return fail(MICKEY_E_ARG, "output %zu of a 32-bit layout is not 4-byte aligned", k);
     }
   }
   if (!any) return ok();                              // nothing to generate
+  // Equal lengths at the packed offsets are exactly mickey_generate's
+  // layout ([n][row] or [G][n_bits]): take the keystream launch.
+  if (equal_packed(n, n_bits, out_offsets, layout)) {
+    const int rc = launch_generate(s, n_bits[0], out, layout);
+    if (rc) return rc;
+    for (auto &p : s->pos) p += n_bits[0];
+    return ok();
+  }
+  // The lengths and offsets reach the kernel through one of two pinned
+  // buffers (so that the copy is a DMA and the next call can fill the other
+  // buffer while this one is in flight) and one device buffer.
   const size_t words = n + n_off;
   if (s->ragged_words < words) {
-    if (s->d_ragged) {
-      CUDA_TRY(cudaStreamSynchronize(s->stream), "sync");
-      cudaFree(s->d_ragged);
-      s->d_ragged = nullptr;
-      s->ragged_words = 0;
+    if (s->ev_ragged) CUDA_TRY(cudaEventSynchronize(s->ev_ragged), "sync");
+    for (int k = 0; k < 2; ++k) {
+      if (s->ev_h2d[k]) CUDA_TRY(cudaEventSynchronize(s->ev_h2d[k]), "sync");
+      if (s->h_ragged[k]) cudaFreeHost(s->h_ragged[k]);
+      s->h_ragged[k] = nullptr;
     }
+    cudaFree(s->d_ragged);
+    s->d_ragged = nullptr;
+    s->ragged_words = 0;
     CUDA_TRY(cudaMalloc(&s->d_ragged, words * 8), "cudaMalloc(ragged lengths)");
+    for (int k = 0; k < 2; ++k)
+      CUDA_TRY(cudaMallocHost(&s->h_ragged[k], words * 8), "cudaMallocHost(ragged lengths)");
     s->ragged_words = words;
   }
+  for (int k = 0; k < 2; ++k)
+    if (!s->ev_h2d[k])
+      CUDA_TRY(cudaEventCreateWithFlags(&s->ev_h2d[k], cudaEventDisableTiming), "event");
   if (!s->ev_ragged)
     CUDA_TRY(cudaEventCreateWithFlags(&s->ev_ragged, cudaEventDisableTiming), "event");
-  // the previous ragged launch (perhaps on another stream) has read its copy
+  const int kb = s->ragged_flip;
+  CUDA_TRY(cudaEventSynchronize(s->ev_h2d[kb]), "staging buffer");  // its last copy is done
+  uint64_t *h = s->h_ragged[kb];
+  std::copy(n_bits, n_bits + n, h);
+  if (out_offsets)
+    std::copy(out_offsets, out_offsets + n_off, h + n);
+  else
+    ragged_packed(n, n_bits, layout, h + n);
+  // the previous ragged launch (perhaps on another stream) has read d_ragged
   CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_ragged, 0), "wait");
-  CUDA_TRY(cudaMemcpyAsync(s->d_ragged, h.data(), words * 8, cudaMemcpyHostToDevice, s->stream),
+  CUDA_TRY(cudaMemcpyAsync(s->d_ragged, h, words * 8, cudaMemcpyHostToDevice, s->stream),
            "H2D ragged lengths");
+  CUDA_TRY(cudaEventRecord(s->ev_h2d[kb], s->stream), "record");
+  s->ragged_flip = kb ^ 1;
   RaggedArgs ra{s->d_state, s->G, s->Gpad, n, s->d_ragged, s->d_ragged + n,
                 static_cast<uint8_t *>(out)};
   CUDA_TRY(launch_ragged(ra, layout, s->stream), "ragged_kernel launch");
@@ -466,9 +519,9 @@ size_t mickey_ragged_output_bytes(size_t n, const uint64_t *n_bits, int layout) 
   if (layout != MICKEY_LAYOUT_BITSLICED_U32 && layout != MICKEY_LAYOUT_BYTES &&
       layout != MICKEY_LAYOUT_U32)
     return 0;
-  if (layout == MICKEY_LAYOUT_U32)
-    for (size_t i = 0; i < n; ++i)
-      if (n_bits[i] % 32) return 0;
+  for (size_t i = 0; i < n; ++i)   // above the per-call limit, or the sum could wrap
+    if (n_bits[i] > kMaxBitsPerCall || (layout == MICKEY_LAYOUT_U32 && n_bits[i] % 32))
+      return 0;
   return size_t(ragged_packed(n, n_bits, layout, nullptr));
 }
 

@@ -12,16 +12,22 @@
 //     has to stop at the row's last byte;
 //   * a lane's state must be the one after exactly its own number of clocks.
 //     When the group starts, the bits of every lane with a length above 0
-//     are cleared in the state in HBM; at each distinct end point E of the
-//     group (at most 32) the current words, masked to the lanes ending at E,
-//     are OR-ed in (one fire-and-forget atomic per word, so the clock loop
-//     does not wait for memory), or stored outright when those lanes are all
-//     the group's lanes.  Lanes asked for 0 bits are never touched.
-// Every tile runs the unrolled clock loop with the previous tile's emission
-// interleaved (as the keystream kernels do); an end point is a branch after
-// its clock, taken by the threads concerned only.  The last
-// tile is clocked in full: past the longest lane every lane has been written
-// back and the extra keystream bits are zero and not stored.
+//     are cleared in the state in HBM (unless all lanes share one length);
+//     at each distinct end point E of the group (at most 32) the current
+//     words, masked to the lanes ending at E, are OR-ed in (one fire-and-
+//     forget atomic per word, so the clock loop does not wait for memory),
+//     or stored outright when those lanes are all the group's lanes.  Lanes
+//     asked for 0 bits are never touched.
+// The clock loop takes one clock per iteration, so that the write-back code
+// exists once: a thread that takes it holds up its warp, and unrolled copies
+// of it were instruction-cache misses each time.  The values the next clock
+// reads besides neighbouring bits (control bit, feedback bits) are computed
+// inside the iteration, so the loop's back edge does not wait on them.  An
+// end point is found from a per-tile mask of the clocks at which some lane
+// ends; the lanes ending there are looked up only then.  Every fourth clock
+// emits one eighth of the previous tile (as the keystream kernels do).  The
+// last tile is clocked in full: past the longest lane every lane has been
+// written back and the extra keystream bits are zero and not stored.
 #include "bitslice.cuh"
 #include "internal.h"
 #include "../../include/mickey.h"
@@ -30,7 +36,6 @@ namespace mickey {
 namespace {
 
 constexpr int kRaggedThreads = 64;
-constexpr int kRaggedU = 4;
 
 // Per-thread view of the group's lanes in shared memory: lane l's length at
 // bits[l * kRaggedThreads] and its output row's address at row[l * kRaggedThreads]
@@ -40,24 +45,30 @@ struct LaneTab {
   uint8_t *const *row;
 };
 
-// Smallest length above `after` among the group's lanes (E) and the lanes
-// whose length is exactly E; E = UINT64_MAX when none is left.
-__device__ __forceinline__ uint64_t next_end(const LaneTab &lt, int lanes, uint64_t after,
-                                             uint32_t &mask) {
-  uint64_t e = ~0ull;
-  mask = 0;
+// Bit k set when some lane's length is t0 + k + 1 (its last clock is clock
+// k of the tile starting at call clock t0).
+__device__ __forceinline__ uint32_t tile_ends(const LaneTab &lt, int lanes, uint64_t t0) {
+  uint32_t e = 0;
   for (int l = 0; l < lanes; ++l) {
-    const uint64_t b = lt.bits[l * kRaggedThreads];
-    if (b > after) {
-      if (b < e) {
-        e = b;
-        mask = 1u << l;
-      } else if (b == e) {
-        mask |= 1u << l;
-      }
-    }
+    const uint64_t d = lt.bits[l * kRaggedThreads] - t0 - 1;   // wraps for lengths <= t0
+    if (d < 32) e |= 1u << d;
   }
   return e;
+}
+
+// The lanes whose length is exactly E.
+__device__ __forceinline__ uint32_t lanes_ending(const LaneTab &lt, int lanes, uint64_t E) {
+  uint32_t m = 0;
+  for (int l = 0; l < lanes; ++l) m |= (lt.bits[l * kRaggedThreads] == E ? 1u : 0u) << l;
+  return m;
+}
+
+// True when every lane has length C (then the one end point writes the
+// whole group back with plain stores).
+__device__ __forceinline__ bool same_end(const LaneTab &lt, int lanes, uint64_t C) {
+  for (int l = 0; l < lanes; ++l)
+    if (lt.bits[l * kRaggedThreads] != C) return false;
+  return true;
 }
 
 // Truth table of (a ^ b) & c (operands a, b, c = 0xF0, 0xCC, 0xAA).
@@ -66,9 +77,16 @@ constexpr uint32_t kXorAnd = ((0xF0u ^ 0xCCu) & 0xAAu) & 0xFFu;              // 
 // Merge the lanes in `m` of the current state into the state in HBM
 // (`pad`: lanes past the last instance, whose bits nothing reads).  The bits
 // of every lane with a length above 0 were cleared in HBM when the group
-// started, so setting the ones is enough.
-__device__ __forceinline__ void snapshot(uint32_t *st, size_t P, const uint32_t (&r)[kReg],
+// started, so setting the ones is enough.  The base address and stride
+// pass through an opaque move, so that the 200 word addresses are formed
+// here, when the branch is taken, and are not held live across the clock
+// loop (which spilled).
+__device__ __forceinline__ void snapshot(uint32_t *st0, size_t P0, const uint32_t (&r)[kReg],
                                          const uint32_t (&s)[kReg], uint32_t m, uint32_t pad) {
+  uint32_t *st;
+  size_t P;
+  asm volatile("mov.b64 %0, %1;" : "=l"(st) : "l"(st0));
+  asm volatile("mov.b64 %0, %1;" : "=l"(P) : "l"(P0));
   if ((m | pad) == ~0u) {
 #pragma unroll
     for (int i = 0; i < kReg; ++i) {
@@ -196,9 +214,7 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_kernel(RaggedArgs a) {
     alive |= (b > 0 ? 1u : 0u) << l;
   }
   uint8_t *grow = LAYOUT == MICKEY_LAYOUT_BITSLICED_U32 ? a.out + a.offsets[g] : nullptr;
-  uint32_t m_end = 0;
-  uint64_t next = next_end(lt, lanes, 0, m_end);
-  if (next == ~0ull) return;                  // every lane asks for 0 bits
+  if (alive == 0) return;                     // every lane asks for 0 bits
 
   const size_t P = a.Gpad;
   uint32_t *st = a.state + g;
@@ -208,37 +224,36 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_kernel(RaggedArgs a) {
     r[i] = st[size_t(i) * P];
     s[i] = st[size_t(kReg + i) * P];
   }
-  // Unless every lane ends at the first end point (one plain store of the
-  // whole group), the end points OR their lanes' words in: clear those lanes.
-  if ((m_end | pad) != ~0u) {
+  // Unless every lane has the same length (one plain store of the whole group
+  // at the end), the end points OR their lanes' words in: clear those lanes.
+  if (!same_end(lt, lanes, C)) {
 #pragma unroll 1
     for (int i = 0; i < 2 * kReg; ++i) atomicAnd(st + size_t(i) * P, ~alive);
   }
   uint32_t *zb0 = zs + threadIdx.x, *zb1 = zs + 32 * kRaggedThreads + threadIdx.x;
-  const uint64_t NT = (C + 31) >> 5;
+  KgFeed fd = kg_feed<false>(r, s, 0u);
+  const uint32_t NT = uint32_t((C + 31) >> 5);      // lengths are at most 2^34
 #pragma unroll 1
-  for (uint64_t T = 0; T < NT; ++T) {
-    const uint64_t t0 = T << 5;
+  for (uint32_t T = 0; T < NT; ++T) {
+    const uint64_t t0 = uint64_t(T) << 5;
     uint32_t *cur = (T & 1) ? zb1 : zb0, *prev = (T & 1) ? zb0 : zb1;
-    int e_in = end_in_tile(next, t0);
+    const uint32_t ends = tile_ends(lt, lanes, t0);
 #pragma unroll 1
-    for (int c = 0; c < 32; c += kRaggedU) {
-#pragma unroll
-      for (int u = 0; u < kRaggedU; ++u) {
-        cur[(c + u) * kRaggedThreads] = lop3<kXorAnd>(r[0], s[0], alive);  // (r0 ^ s0) & alive
-        clock_kg<false, false>(r, s, 0u, 0u);
-        if (c + u == e_in) {                   // lanes m_end have run their length
-          snapshot(st, P, r, s, m_end, pad);
-          alive &= ~m_end;
-          next = next_end(lt, lanes, next, m_end);
-          e_in = end_in_tile(next, t0);
-        }
+    for (int c = 0; c < 32; ++c) {
+      cur[c * kRaggedThreads] = lop3<kXorAnd>(r[0], s[0], alive);  // (r0 ^ s0) & alive
+      clock_kg_from<false>(r, s, fd, 0u);
+      fd = kg_feed<false>(r, s, 0u);         // the next clock's, inside this iteration
+      if ((ends >> c) & 1u) {                  // some lanes have run their length
+        const uint32_t m = lanes_ending(lt, lanes, t0 + c + 1);
+        snapshot(st, P, r, s, m, pad);
+        alive &= ~m;
       }
-      if (T > 0) ragged_slice<LAYOUT>(prev, lt, grow, lanes, t0 - 32, 32, C, c >> 2);
+      if ((c & 3) == 3 && T > 0)
+        ragged_slice<LAYOUT>(prev, lt, grow, lanes, t0 - 32, 32, C, c >> 2);
     }
   }
   // the last tile (possibly partial)
-  const uint64_t tl = (NT - 1) << 5;
+  const uint64_t tl = uint64_t(NT - 1) << 5;
   ragged_tile<LAYOUT>(((NT - 1) & 1) ? zb1 : zb0, lt, grow, lanes, tl,
                       C - tl >= 32 ? 32 : int(C - tl), C);
 }

@@ -116,6 +116,8 @@ def main():
         rng = np.random.default_rng(1)
         nb = np.full(a.n, a.n_bits, np.uint64)
         if a.spread:
+            if not 0 < a.spread <= a.n_bits:
+                raise SystemExit("--spread must be in [0, n_bits]")
             nb = rng.integers(a.n_bits - a.spread, a.n_bits + 1, a.n).astype(np.uint64)
         out = None
         for _ in range(a.reps):

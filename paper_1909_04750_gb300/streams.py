@@ -99,7 +99,8 @@ class Streams:
         if offsets is None:
             total = int(self._L.mickey_ragged_output_bytes(self.n, nb.ctypes.data, lay))
             if total == 0 and nb.any():
-                raise N.MickeyError(N.E_LAYOUT, "layout cannot hold these lengths")
+                raise N.MickeyError(N.E_ARG, "lengths invalid for this layout (u32 needs multiples "
+                                               "of 32; at most 2^34 bits per call)")
             if out is None:
                 out = torch.empty(max(total, 16), dtype=torch.uint8, device="cuda")
             elif out.numel() * out.element_size() < total:

@@ -195,6 +195,12 @@ def test_ragged_host_side_errors_and_sizes(L):
     assert L.mickey_ragged_output_bytes(3, w.ctypes.data, N.LAYOUT_U32) == 12
     assert L.mickey_ragged_output_bytes(3, w.ctypes.data, N.LAYOUT_U32_F32) == 0
     assert L.mickey_ragged_output_bytes(3, None, N.LAYOUT_BYTES) == 0
+    # a length above the per-call limit (e.g. a negative length cast to
+    # uint64) is refused rather than wrapping the sum
+    big = np.array([1 << 34, (1 << 34) + 1, 2**64 - 4096], np.uint64)
+    assert L.mickey_ragged_output_bytes(1, big.ctypes.data, N.LAYOUT_BYTES) == (1 << 31)
+    for lay in (N.LAYOUT_BYTES, N.LAYOUT_BITSLICED_U32, N.LAYOUT_U32):
+        assert L.mickey_ragged_output_bytes(3, big.ctypes.data, lay) == 0
 
 
 def test_packed_offsets_match_library_sizes(L):

@@ -149,6 +149,55 @@ def test_ragged_explicit_offsets_leave_gaps_untouched():
     assert np.all(host[mask] == 0xA5)
 
 
+@pytest.mark.parametrize("layout,b", [("bytes", 1001), ("u32", 1024), ("bitsliced", 1001)])
+@pytest.mark.parametrize("offsets", ["none", "packed", "gapped"])
+def test_ragged_equal_lengths(layout, b, offsets):
+    """Equal lengths: at the packed offsets the call is one keystream launch
+    (the plain generate's layout); at other offsets the ragged kernel's
+    all-lanes-end-together write-back.  Both against the oracle, then a
+    continuation."""
+    n = 100
+    s = workloads.batched(n)
+    nb = np.full(n, b, np.uint64)
+    st = _streams(s)
+    G = (n + 31) // 32
+    if layout == "bitsliced":
+        step, n_off = 4 * b, G
+    else:
+        step, n_off = (b // 8 if layout == "u32" else (b + 7) // 8), n
+    gap = 16 if offsets == "gapped" else 0
+    offs = np.arange(n_off, dtype=np.uint64) * np.uint64(step + gap)
+    total = int(offs[-1]) + step + 16
+    out = torch.full((total,), 0xA5, dtype=torch.uint8, device="cuda")
+    st.generate_ragged(nb, layout, out=out, offsets=None if offsets == "none" else offs)
+    K = 96
+    cont = st.generate(K, "bytes").cpu().numpy()
+    host = out.cpu().numpy()
+    st.sync()
+    ref = _bits(s, np.full(n, b + K, np.uint64))
+    if layout == "bitsliced":
+        for g in range(G):
+            words = host[int(offs[g]):int(offs[g]) + 4 * b].view(np.uint32)
+            for i in range(32 * g, min(n, 32 * g + 32)):
+                got = ((words >> np.uint32(i - 32 * g)) & 1).astype(np.uint8)
+                assert np.array_equal(got, ref[i][:b]), (g, i)
+    else:
+        for i in range(n):
+            row = host[int(offs[i]):int(offs[i]) + step]
+            want = _pack(ref[i][:b])
+            if layout == "u32":
+                want = want.view(">u4").astype(np.uint32).view(np.uint8)
+            assert np.array_equal(row, want), i
+    for i in range(n):
+        assert np.array_equal(cont[i], _pack(ref[i][b:])), i
+        assert st.position(i) == b + K
+    if offsets == "gapped":                    # the gaps keep their sentinel
+        mask = np.ones(total, bool)
+        for k in range(n_off):
+            mask[int(offs[k]):int(offs[k]) + step] = False
+        assert np.all(host[mask] == 0xA5)
+
+
 def test_ragged_twice_and_export_state():
     n = 96
     s = workloads.batched(n)
