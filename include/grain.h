@@ -25,7 +25,8 @@
  *           each chunk continuing from the state its predecessor published
  *           (a bounded wait: MICKEY_SPIN_LIMIT polls of about 256 ns, after
  *           which grain_sync reports MICKEY_E_TIMEOUT).  MICKEY_GRAIN_QUEUE=1,
- *           read when a handle is created, forces the queue.
+ *           read when a handle is created, forces the queue.  The bytes
+ *           layout stages rows in tensor memory (one block of 8 warps per SM).
  */
 #ifndef GRAIN_H
 #define GRAIN_H

@@ -23,8 +23,12 @@
 // (two bodies of 80 clocks fill five 32-clock tiles); after each body the
 // finished tiles are emitted: as they are (bitsliced layout) or, for
 // row-major bytes, transposed by the two-pass in-place block swaps also used
-// for MICKEY and bit-reversed, since Grain's bytes hold the first keystream
-// bit in the least significant bit.
+// for MICKEY, on the tile's rows in reverse order, since Grain's bytes hold
+// the first keystream bit in the least significant bit.  The bytes layout
+// stages eight tiles of every row so that each row goes out as whole
+// 32-byte sectors; the staging (1 KiB per thread) lives in tensor memory,
+// not shared memory, so that the shared memory of an SM (the rings) holds
+// two warps per SM sub-partition.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,43 +73,128 @@ struct GrainQueue {
 };
 
 // Row staging of the bytes layout: the transposed words of 8 consecutive
-// tiles per lane, [lane][thread][8] words, so that each row goes out as one
-// whole 32-byte sector (two 16-byte stores) instead of 4-byte pieces.
+// tiles per lane, so that each row goes out as one whole 32-byte sector (two
+// 16-byte stores) instead of 4-byte pieces.
 constexpr int kStage = 8;
 
-// Emit the 32-clock tile k of the call (clocks 32k .. 32k+nb-1) held in zb
-// (word c = clock 32k + c, bit l = lane l) of group g.  Bitsliced: stored as
-// it is.  Bytes: transposed and staged in rb; the staged tiles are written
-// out after the last tile of each aligned block of 8 and after the call's
-// last tile.
+// Blocks of the bytes layout: eight warps, two per lane quarter of tensor
+// memory (warp w: lanes 32 (w % 4) .. + 31, columns 256 (w / 4) .. + 255).
+// A kernel that allocates tensor memory runs one block per SM (that is what
+// the occupancy calculator answers for it, whatever its other resources),
+// so the block takes all 512 columns of the SM; its rings fill 160 KiB of
+// shared memory and its 256 threads the register file.
+constexpr int kGrainBytesThreads = 256;
+constexpr uint32_t kTmemCols = 512;
+
 template <int LAYOUT>
-__device__ __forceinline__ void grain_emit(uint32_t *zb, uint32_t *rb, const GrainArgs &a,
+__host__ __device__ constexpr int grain_threads() {
+  return LAYOUT == MICKEY_LAYOUT_BYTES ? kGrainBytesThreads : kGrainThreads;
+}
+
+// Tensor memory (TMEM) used as plain storage: a block allocates columns, a
+// warp reads and writes 32-bit words of its own 32 lanes (lane = the
+// thread's lane, lanes 32 (warp % 4) .. + 31) with warp-wide instructions.
+// Address: lane in bits 31..16, column in bits 15..0.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t v0, uint32_t v1, uint32_t v2,
+                                         uint32_t v3) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+               :: "r"(taddr), "r"(v0), "r"(v1), "r"(v2), "r"(v3) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// Columns taddr .. taddr + 15 of the thread's lane; returns once they are in
+// registers (the load and its wait in one statement, so that no use of the
+// registers can be scheduled before the wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&w)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+        "=r"(w[7]), "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]),
+        "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Bytes layout: warp 0 allocates the block's columns (the address goes
+// through shared memory to every warp); returns the warp's base address
+// (its lane quarter and its 256 columns).  Other layouts use no tensor memory.
+template <int LAYOUT>
+__device__ __forceinline__ uint32_t tmem_open(uint32_t *slot) {
+  if constexpr (LAYOUT == MICKEY_LAYOUT_BYTES) {
+    if (threadIdx.x < 32) {
+      const uint32_t dst = uint32_t(__cvta_generic_to_shared(slot));
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                   :: "r"(dst), "r"(kTmemCols) : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t warp = threadIdx.x >> 5;
+    return *slot + (((warp & 3u) * 32u) << 16) + (warp >> 2) * 256u;
+  } else {
+    return 0;
+  }
+}
+
+// Every warp's tensor-memory accesses have completed; warp 0 frees the columns.
+template <int LAYOUT>
+__device__ __forceinline__ void tmem_close(const uint32_t *slot) {
+  if constexpr (LAYOUT == MICKEY_LAYOUT_BYTES) {
+    __syncwarp();
+    tmem_wait_st();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                   :: "r"(*slot), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Emit the 32-clock tile k of the call (clocks 32k .. 32k+nb-1) held in zb
+// (word c = clock 32k + c, bit l = lane l; stride kRingStride) of group g.
+// Bitsliced: stored as it is.  Bytes: transposed and staged in tensor memory
+// at tm (the warp's lanes, 256 columns: column 32r + 4 slot + q holds the
+// word of lane 31 - r - 8q for the tile in staging slot k % 8); the staged
+// tiles are written out after the last tile of each aligned block of 8 and
+// after the call's last tile.  The bytes path runs warp-wide instructions:
+// every lane of the warp takes it, lanes outside `mask` store nothing.
+template <int LAYOUT>
+__device__ __forceinline__ void grain_emit(uint32_t *zb, uint32_t tm, const GrainArgs &a,
                                            uint32_t g, uint64_t k, int nb, uint32_t mask) {
-  constexpr int T = kGrainThreads;
+  constexpr int S = kRingStride;
   const uint64_t t0 = k << 5;
-  if (mask == 0) return;                   // a lane past the last group: nothing to store
   if constexpr (LAYOUT == MICKEY_LAYOUT_BITSLICED_U32) {
+    if (mask == 0) return;                 // a lane past the last group: nothing to store
     uint32_t *o = static_cast<uint32_t *>(a.out) + size_t(g) * a.n_bits + t0;
     if (nb == 32 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         uint4 v;
-        v.x = zb[(4 * j + 0) * T] & mask;
-        v.y = zb[(4 * j + 1) * T] & mask;
-        v.z = zb[(4 * j + 2) * T] & mask;
-        v.w = zb[(4 * j + 3) * T] & mask;
+        v.x = zb[(4 * j + 0) * S] & mask;
+        v.y = zb[(4 * j + 1) * S] & mask;
+        v.z = zb[(4 * j + 2) * S] & mask;
+        v.w = zb[(4 * j + 3) * S] & mask;
         reinterpret_cast<uint4 *>(o)[j] = v;
       }
     } else {
-      for (int c = 0; c < nb; ++c) o[c] = zb[c * T] & mask;
+      for (int c = 0; c < nb; ++c) o[c] = zb[c * S] & mask;
     }
   } else {
+    // The tile is transposed with its rows taken in reverse order (row i =
+    // clock 31 - i): the transposed row of lane l then holds clock c in bit
+    // c, the order of Grain's bytes (first keystream bit in the least
+    // significant bit), with no bit reversal.
     // pass 1: block swaps of size 4, 2, 1 within each 8 rows
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
       uint32_t v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = zb[(8 * j + q) * T];
+      for (int q = 0; q < 8; ++q) v[q] = zb[(31 - 8 * j - q) * S];
       swap_bits<4>(v[0], v[4]); swap_bits<4>(v[1], v[5]);
       swap_bits<4>(v[2], v[6]); swap_bits<4>(v[3], v[7]);
       swap_bits<2>(v[0], v[2]); swap_bits<2>(v[1], v[3]);
@@ -113,44 +202,55 @@ __device__ __forceinline__ void grain_emit(uint32_t *zb, uint32_t *rb, const Gra
       swap_bits<1>(v[0], v[1]); swap_bits<1>(v[2], v[3]);
       swap_bits<1>(v[4], v[5]); swap_bits<1>(v[6], v[7]);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) zb[(8 * j + q) * T] = v[q];
+      for (int q = 0; q < 8; ++q) zb[(31 - 8 * j - q) * S] = v[q];
     }
-    // pass 2: block swaps of size 16 and 8; row k + 8q is lane 31 - k - 8q,
-    // its word has the tile's first clock in bit 31, which Grain's bytes
-    // take in bit 0 (bit reversal)
+    // pass 2: block swaps of size 16 and 8; row r + 8q is lane 31 - r - 8q
     const int slot = int(k & (kStage - 1));
+    __syncwarp();
 #pragma unroll 1
     for (int r = 0; r < 8; ++r) {
       uint32_t v[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = zb[(r + 8 * q) * T];
+      for (int q = 0; q < 4; ++q) v[q] = zb[(31 - r - 8 * q) * S];
       swap_halves(v[0], v[2]);
       swap_halves(v[1], v[3]);
       swap_bytes<false>(v[0], v[1]);
       swap_bytes<false>(v[2], v[3]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) rb[(31 - r - 8 * q) * (T * kStage) + slot] = __brev(v[q]);
+      tmem_st4(tm + uint32_t(32 * r + 4 * slot), v[0], v[1], v[2], v[3]);
     }
     const bool last = t0 + uint64_t(nb) >= a.n_bits;
     if (slot == kStage - 1 || last) {
       // write tiles k - slot .. k of every valid lane
+      tmem_wait_st();
       const uint32_t pitch = uint32_t((a.n_bits + 7) >> 3);
       const uint64_t kA = k - uint64_t(slot);
       uint8_t *base = static_cast<uint8_t *>(a.out) + 32ull * g * pitch + kA * 4;
       const bool sector = slot == kStage - 1 && nb == 32 && (pitch & 15u) == 0 &&
                           (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;
+      // bytes of the staged block that belong to the call
+      const uint64_t bytes = ((kA << 5) + ((uint64_t(slot) << 5) + uint64_t(nb)) + 7) / 8 -
+                             ((kA << 5) >> 3);
 #pragma unroll 1
-      for (int l = 0; l < 32; ++l) {
-        if (!((mask >> l) & 1u)) continue;
-        const uint32_t *src = rb + l * (T * kStage);
-        uint8_t *o = base + uint64_t(uint32_t(l) * pitch);
-        if (sector) {
-          reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(src)[0];
-          reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(src)[1];
-        } else {
-          const uint64_t bytes = ((kA << 5) + ((uint64_t(slot) << 5) + uint64_t(nb)) + 7) / 8 -
-                                 ((kA << 5) >> 3);
-          for (uint64_t by = 0; by < bytes; ++by) o[by] = uint8_t(src[by >> 2] >> (8 * (by & 3)));
+      for (int r = 0; r < 8; ++r) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {            // slots 4h .. 4h + 3: bytes 16h .. 16h + 15
+          uint32_t w[16];                        // w[4 j + q]: slot 4h + j of lane 31 - r - 8q
+          __syncwarp();
+          tmem_ld16(tm + uint32_t(32 * r + 16 * h), w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int l = 31 - r - 8 * q;
+            if (!((mask >> l) & 1u)) continue;
+            uint8_t *o = base + uint64_t(uint32_t(l) * pitch) + 16 * h;
+            if (sector) {
+              *reinterpret_cast<uint4 *>(o) = make_uint4(w[q], w[4 + q], w[8 + q], w[12 + q]);
+            } else {
+#pragma unroll
+              for (int by = 0; by < 16; ++by)
+                if (uint64_t(16 * h + by) < bytes)
+                  o[by] = uint8_t(w[4 * (by >> 2) + q] >> (8 * (by & 3)));
+            }
+          }
         }
       }
     }
@@ -164,7 +264,7 @@ __device__ __forceinline__ void grain_emit(uint32_t *zb, uint32_t *rb, const Gra
 template <int LAYOUT>
 __device__ __forceinline__ void grain_piece(const GrainArgs &a, uint32_t g, bool live,
                                             uint64_t t_a, uint64_t t_b, uint32_t *zb,
-                                            uint32_t *rb) {
+                                            uint32_t tm) {
   const size_t P = a.Gpad;
   const uint32_t gs = live ? g : 0;
   uint32_t s[kG], b[kG];
@@ -179,25 +279,25 @@ __device__ __forceinline__ void grain_piece(const GrainArgs &a, uint32_t g, bool
   uint64_t emitted = 0;                     // tiles of this piece emitted so far
 #pragma unroll 1
   for (uint64_t j = 0; j < full; ++j) {
-    grain_body<false>(s, b, zb + (j & 1) * kG * kGrainThreads);
+    grain_body<false>(s, b, zb + (j & 1) * kG * kRingStride);
     const uint64_t done = (j + 1) * kG;
 #pragma unroll 1
     for (; (emitted + 1) * 32 <= done; ++emitted)
-      grain_emit<LAYOUT>(zb + ((emitted * 32) % kRing) * kGrainThreads, rb, a, g,
+      grain_emit<LAYOUT>(zb + ((emitted * 32) % kRing) * kRingStride, tm, a, g,
                          (t_a >> 5) + emitted, 32, mask);
   }
   const int rem = int(n - full * kG);
   if (rem) {
-    uint32_t *zt = zb + (full & 1) * kG * kGrainThreads;
+    uint32_t *zt = zb + (full & 1) * kG * kRingStride;
 #pragma unroll 1
-    for (int c = 0; c < rem; ++c) zt[c * kGrainThreads] = grain_clock_shift(s, b);
+    for (int c = 0; c < rem; ++c) zt[c * kRingStride] = grain_clock_shift(s, b);
   }
 #pragma unroll 1
   for (; emitted * 32 < n; ++emitted) {
     const int nb = int(min(uint64_t(32), n - emitted * 32));
-    uint32_t *zt = zb + ((emitted * 32) % kRing) * kGrainThreads;
-    for (int c = nb; c < 32; ++c) zt[c * kGrainThreads] = 0u;   // past the call's last clock
-    grain_emit<LAYOUT>(zt, rb, a, g, (t_a >> 5) + emitted, nb, mask);
+    uint32_t *zt = zb + ((emitted * 32) % kRing) * kRingStride;
+    for (int c = nb; c < 32; ++c) zt[c * kRingStride] = 0u;   // past the call's last clock
+    grain_emit<LAYOUT>(zt, tm, a, g, (t_a >> 5) + emitted, nb, mask);
   }
   if (live) {
 #pragma unroll
@@ -228,13 +328,15 @@ __device__ __forceinline__ void grain_store_release(uint32_t *p, uint32_t v) {
 // output and state are then undefined, and grain_sync reports it).  Every SM
 // sub-partition keeps its full share of warps until the queue runs dry.
 template <int LAYOUT>
-__global__ void __launch_bounds__(kGrainThreads) grain_keystream_kernel(GrainArgs a, GrainQueue q) {
-  // shared memory: the keystream ring (kRing words per thread, [word][thread])
-  // and, for the bytes layout, the row staging ([lane][thread][8])
+__global__ void __launch_bounds__(grain_threads<LAYOUT>())
+    grain_keystream_kernel(GrainArgs a, GrainQueue q) {
+  // shared memory: each warp's keystream ring (kRing words per thread,
+  // [word][lane]); the bytes layout's row staging is in tensor memory
   extern __shared__ __align__(16) uint32_t ring[];
+  __shared__ uint32_t tmem_slot;
   const uint32_t lane = threadIdx.x & 31u;
-  uint32_t *zb = ring + threadIdx.x;
-  uint32_t *rb = ring + kRing * kGrainThreads + threadIdx.x * kStage;
+  uint32_t *zb = ring + (threadIdx.x >> 5) * (kRing * kRingStride) + lane;
+  const uint32_t tm = tmem_open<LAYOUT>(&tmem_slot);
   const uint64_t items = uint64_t(q.W) * q.n_chunks;
 #pragma unroll 1
   for (;;) {
@@ -261,11 +363,12 @@ __global__ void __launch_bounds__(kGrainThreads) grain_keystream_kernel(GrainArg
     const uint32_t g = w * 32 + lane;
     const uint64_t t_a = uint64_t(k) * q.chunk;
     const uint64_t t_b = min(a.n_bits, t_a + q.chunk);
-    grain_piece<LAYOUT>(a, g, g < a.G, t_a, t_b, zb, rb);
+    grain_piece<LAYOUT>(a, g, g < a.G, t_a, t_b, zb, tm);
     __threadfence();
     __syncwarp();
     if (lane == 0) grain_store_release(q.flags + w, k + 1);
   }
+  tmem_close<LAYOUT>(&tmem_slot);
 }
 
 // ---------------------------------------------------------------- init
@@ -375,43 +478,67 @@ __global__ void __launch_bounds__(kInitT) grain_init_kernel(GrainInitArgs a) {
 // in the resident warps at once, so that the queue would add waits and no
 // parallelism: a warp-group's chunks cannot overlap).
 template <int LAYOUT>
-__global__ void __launch_bounds__(kGrainThreads) grain_grid_kernel(GrainArgs a) {
+__global__ void __launch_bounds__(grain_threads<LAYOUT>()) grain_grid_kernel(GrainArgs a) {
   extern __shared__ __align__(16) uint32_t ring[];
+  __shared__ uint32_t tmem_slot;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t tm = tmem_open<LAYOUT>(&tmem_slot);
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.G) return;
-  grain_piece<LAYOUT>(a, g, true, 0, a.n_bits, ring + threadIdx.x,
-                      ring + kRing * kGrainThreads + threadIdx.x * kStage);
+  if (g - lane < a.G)   // the warp holds a group; its lanes past the last group store nothing
+    grain_piece<LAYOUT>(a, g, g < a.G, 0, a.n_bits,
+                        ring + (threadIdx.x >> 5) * (kRing * kRingStride) + lane, tm);
+  tmem_close<LAYOUT>(&tmem_slot);
 }
 
 template <int LAYOUT>
 cudaError_t launch_grain_layout(const GrainArgs &a, const GrainQueue &q, int sm_count,
-                                bool force_queue, cudaStream_t st) {
-  const size_t smem = size_t(kRing) * kGrainThreads * 4 +
-                      (LAYOUT == MICKEY_LAYOUT_BYTES ? size_t(32) * kGrainThreads * kStage * 4 : 0);
+                                int force, cudaStream_t st) {
+  constexpr int T = grain_threads<LAYOUT>();
+  const size_t smem = size_t(kRing) * T * 4;
   cudaError_t e = cudaFuncSetAttribute(grain_keystream_kernel<LAYOUT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grain_keystream_kernel<LAYOUT>,
-                                                    kGrainThreads, smem);
+  e = cudaFuncSetAttribute(grain_grid_kernel<LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(smem));
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const uint64_t slots = uint64_t(per_sm) * sm_count * (kGrainThreads / 32);
-  if (q.W <= slots && !force_queue) {   // every warp-group gets a warp of its own
-    e = cudaFuncSetAttribute(grain_grid_kernel<LAYOUT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    grain_grid_kernel<LAYOUT><<<(a.G + kGrainThreads - 1) / kGrainThreads, kGrainThreads, smem,
-                                st>>>(a);
+  // the rings of two blocks need the largest shared-memory carveout
+  e = cudaFuncSetAttribute(grain_keystream_kernel<LAYOUT>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout,
+                           int(cudaSharedmemCarveoutMaxShared));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(grain_grid_kernel<LAYOUT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           int(cudaSharedmemCarveoutMaxShared));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, per_sm_grid = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grain_keystream_kernel<LAYOUT>, T,
+                                                    smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_grid, grain_grid_kernel<LAYOUT>, T,
+                                                    smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1 || per_sm_grid < 1) return cudaErrorInvalidConfiguration;
+  // the blocks resident on an SM must never ask for more tensor memory than it
+  // has (an allocation that cannot be met waits)
+  if (LAYOUT == MICKEY_LAYOUT_BYTES &&
+      uint32_t(std::max(per_sm, per_sm_grid)) * kTmemCols > 512u)
+    return cudaErrorInvalidConfiguration;
+  // The grid launch when every warp-group gets a warp of its own, even if
+  // some SMs then get no block: a warp-group's clocks are one sequential
+  // chain, so spreading chunks over more warps (the queue) only adds waits
+  // (2^20 bytes-layout instances: 6.9 Tbit/s on 128 SMs against 5.7 through
+  // the queue on all 152).  `force` = 1: always the queue.
+  const uint64_t slots = uint64_t(per_sm) * sm_count * (T / 32);
+  if (q.W <= slots && force != 1) {
+    grain_grid_kernel<LAYOUT><<<(a.G + T - 1) / T, T, smem, st>>>(a);
     return cudaGetLastError();
   }
   // every block resident (the waits need it); no more warps than items
   const uint64_t items = uint64_t(q.W) * q.n_chunks;
-  const uint64_t want = (items + kGrainThreads / 32 - 1) / (kGrainThreads / 32);
+  const uint64_t want = (items + T / 32 - 1) / (T / 32);
   const uint32_t blocks = uint32_t(std::min<uint64_t>(uint64_t(per_sm) * sm_count, want));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(kGrainThreads);
+  cfg.blockDim = dim3(T);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -443,7 +570,8 @@ struct grain_streams {
   uint64_t pos = 0;
   int sm_count = 0;
   uint32_t spin_limit = 1u << 24;
-  bool force_queue = false;      // MICKEY_GRAIN_QUEUE=1: always the queue-fed launch
+  int force = -1;                // MICKEY_GRAIN_QUEUE=1: always the queue-fed launch,
+                                 // =0 (the default): the grid launch when every warp-group fits
 };
 
 namespace {
@@ -499,7 +627,7 @@ MICKEY_API grain_streams *grain_init_streams(const void *keys, const void *ivs, 
     const long long l = atoll(v);
     if (l > 0 && l < (1ll << 31)) s->spin_limit = uint32_t(l);
   }
-  if (const char *v = getenv("MICKEY_GRAIN_QUEUE")) s->force_queue = atoi(v) != 0;
+  if (const char *v = getenv("MICKEY_GRAIN_QUEUE")) s->force = atoi(v) != 0 ? 1 : 0;
   if (ok && mem == MICKEY_MEM_HOST) {
     ok = cudaMalloc(&s->d_inputs, n * 18) == cudaSuccess &&
          cudaMemcpyAsync(s->d_inputs, keys, n * 10, cudaMemcpyHostToDevice, s->stream) ==
@@ -562,8 +690,8 @@ MICKEY_API int grain_generate(grain_streams *s, uint64_t n_bits, void *out, int 
     return grain_fail(MICKEY_E_CUDA, "queue reset");
   const cudaError_t e =
       layout == MICKEY_LAYOUT_BYTES
-          ? launch_grain_layout<MICKEY_LAYOUT_BYTES>(a, q, s->sm_count, s->force_queue, s->stream)
-          : launch_grain_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, q, s->sm_count, s->force_queue,
+          ? launch_grain_layout<MICKEY_LAYOUT_BYTES>(a, q, s->sm_count, s->force, s->stream)
+          : launch_grain_layout<MICKEY_LAYOUT_BITSLICED_U32>(a, q, s->sm_count, s->force,
                                                              s->stream);
   if (e != cudaSuccess) return grain_fail(MICKEY_E_CUDA, "grain keystream launch");
   s->pos += n_bits;

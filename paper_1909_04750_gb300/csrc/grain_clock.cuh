@@ -12,8 +12,9 @@ namespace mickey {
 namespace grainc {
 
 constexpr int kG = 80;               // register length
-constexpr int kGrainThreads = 64;    // groups per block
+constexpr int kGrainThreads = 64;    // groups per block (bitsliced layout)
 constexpr int kRing = 160;           // keystream words per thread in the ring
+constexpr int kRingStride = 32;      // each warp's ring is [word][lane]
 
 __device__ __forceinline__ uint32_t xor3(uint32_t a, uint32_t b, uint32_t c) {
   return lop3<0x96>(a, b, c);
@@ -83,13 +84,13 @@ __device__ __forceinline__ uint32_t grain_clock(uint32_t (&s)[kG], uint32_t (&b)
   return z;
 }
 
-// 80 clocks (one full rotation); keystream word of clock c to zb[c * kGrainThreads].
+// 80 clocks (one full rotation); keystream word of clock c to zb[c * kRingStride].
 template <bool INIT>
 __device__ __forceinline__ void grain_body(uint32_t (&s)[kG], uint32_t (&b)[kG], uint32_t *zb) {
   static_for<0, kG>([&](auto rc) {
     constexpr int R = decltype(rc)::value;
     const uint32_t z = grain_clock<R, INIT>(s, b);
-    if constexpr (!INIT) zb[R * kGrainThreads] = z;
+    if constexpr (!INIT) zb[R * kRingStride] = z;
   });
 }
 

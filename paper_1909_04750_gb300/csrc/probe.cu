@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(mickey::grainc::kGrainThreads)
 #pragma unroll 1
   for (int k = 0; k < bodies; ++k) {
     if constexpr (STORE) {
-      grain_body<false>(s, b, zb + threadIdx.x);
+      grain_body<false>(s, b, zb + (threadIdx.x >> 5) * (kG * kRingStride) + (threadIdx.x & 31));
     } else {
       mickey::static_for<0, kG>([&](auto rc) {
         constexpr int R = decltype(rc)::value;

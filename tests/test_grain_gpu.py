@@ -47,6 +47,23 @@ def test_queue_fed_launch_every_instance(monkeypatch, n, n_bits):
     assert np.array_equal(words, og.to_bitsliced(ref, n_bits))
 
 
+@pytest.mark.parametrize("n,n_bits", [(1000, 3000), (9000, 1281), (64, 6000)])
+def test_grid_launch_every_instance(monkeypatch, n, n_bits):
+    # one warp per warp-group for the whole call (the default whenever the
+    # warp-groups fit), also with the override set to it
+    monkeypatch.setenv("MICKEY_GRAIN_QUEUE", "0")
+    s = workloads.grain_streams(n, seed=17)
+    ref = og.batch_bytes(s.keys, s.ivs, n_bits, threads=THREADS)
+    st = _gs(s)
+    got = st.generate(n_bits, "bytes").cpu().numpy()
+    st.sync()
+    assert np.array_equal(got, ref)
+    st2 = _gs(s)
+    words = st2.generate(n_bits, "bitsliced").cpu().numpy().view(np.uint32)
+    st2.sync()
+    assert np.array_equal(words, og.to_bitsliced(ref, n_bits))
+
+
 def test_known_answer_vectors_on_the_gpu():
     from paper_1909_04750_gb300.grain import GrainStreams
     rows = [l.split() for l in open(os.path.join(GOLDEN, "grain_kat.txt"))
