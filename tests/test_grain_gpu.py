@@ -64,6 +64,28 @@ def test_grid_launch_every_instance(monkeypatch, n, n_bits):
     assert np.array_equal(words, og.to_bitsliced(ref, n_bits))
 
 
+@pytest.mark.parametrize("layout", ["bytes", "bitsliced"])
+def test_queue_wait_runs_out_without_a_fault(monkeypatch, layout):
+    # the wait of a chunk for its predecessor is bounded: with one poll of
+    # about 256 ns allowed, every chunk after the first gives up long before
+    # its predecessor (about 1280 clocks) has published, the call still
+    # returns, grain_sync reports the timeout, and the context keeps working
+    # (the bytes layout's blocks also free their tensor memory)
+    monkeypatch.setenv("MICKEY_GRAIN_QUEUE", "1")
+    monkeypatch.setenv("MICKEY_SPIN_LIMIT", "1")
+    s = workloads.grain_streams(3 * 1024 + 17, seed=18)
+    st = _gs(s)
+    st.generate(6000, layout)
+    with pytest.raises(N.MickeyError) as ei:
+        st.sync()
+    assert ei.value.code == N.E_TIMEOUT
+    monkeypatch.delenv("MICKEY_SPIN_LIMIT")
+    ok = _gs(s)
+    got = ok.generate(6000, "bytes").cpu().numpy()
+    ok.sync()
+    assert np.array_equal(got, og.batch_bytes(s.keys, s.ivs, 6000, threads=THREADS))
+
+
 def test_known_answer_vectors_on_the_gpu():
     from paper_1909_04750_gb300.grain import GrainStreams
     rows = [l.split() for l in open(os.path.join(GOLDEN, "grain_kat.txt"))
