@@ -198,17 +198,19 @@ int run_init(mickey_streams *s, const void *keys, const void *ivs,
       for (size_t i = 0; i < n; ++i)
         if (iv_lens[i] > MICKEY_MAX_IV_BITS)
           return fail(MICKEY_E_IVLEN, "iv_lens[%zu] = %u exceeds 80 bits", i, iv_lens[i]);
+    // keys, IVs and lengths each at a 16-byte aligned offset (the init
+    // kernel then reads them with 16-byte loads)
+    const size_t rec = (n * 10 + 15) & ~size_t(15);
     if (!s->d_inputs)
-      CUDA_TRY(cudaMalloc(&s->d_inputs, n * 24), "cudaMalloc(inputs)");
+      CUDA_TRY(cudaMalloc(&s->d_inputs, 2 * rec + n * 4), "cudaMalloc(inputs)");
     uint8_t *p = s->d_inputs;
     CUDA_TRY(cudaMemcpyAsync(p, keys, n * 10, cudaMemcpyHostToDevice, s->stream), "H2D keys");
-    CUDA_TRY(cudaMemcpyAsync(p + n * 10, ivs, n * 10, cudaMemcpyHostToDevice, s->stream),
+    CUDA_TRY(cudaMemcpyAsync(p + rec, ivs, n * 10, cudaMemcpyHostToDevice, s->stream),
              "H2D ivs");
     dk = p;
-    di = p + n * 10;
+    di = p + rec;
     if (iv_lens) {
-      // 4-byte aligned slot after the 20n bytes of keys and IVs
-      uint32_t *lens = reinterpret_cast<uint32_t *>(p + n * 20);
+      uint32_t *lens = reinterpret_cast<uint32_t *>(p + 2 * rec);
       CUDA_TRY(cudaMemcpyAsync(lens, iv_lens, n * 4, cudaMemcpyHostToDevice, s->stream),
                "H2D iv_lens");
       dl = lens;

@@ -5,7 +5,8 @@
 
 ``plain``: creates a handle for ``workloads.plain_scale(n)`` (device
 inputs), then ``--reps`` times re-keys it and generates ``n_bits`` per
-stream in ``layout``.  The launch configuration comes from the environment
+stream in ``layout`` (with ``--continue``, re-keys only before the first
+generation, so that later launches clock no initialisation).  The launch configuration comes from the environment
 (MICKEY_MODE, MICKEY_UNROLL, MICKEY_STAGE) or the library defaults, or with
 ``--autotune`` from the autotuner (as the benchmarks do; its trial launches
 come first).
@@ -53,6 +54,7 @@ def main():
                                       "ragged", "grain"), default="plain")
     p.add_argument("--spread", type=int, default=0)
     p.add_argument("--autotune", action="store_true")
+    p.add_argument("--continue", dest="cont", action="store_true")
     a = p.parse_args()
     build()
     if a.case == "batched":
@@ -145,8 +147,9 @@ def main():
         from . import autotune
         from .streams import layout_id
         print("launch:", autotune.describe(autotune.tune(st, a.n_bits, layout_id(a.layout))))
-    for _ in range(a.reps):
-        st.reset(k, v)
+    for rep in range(a.reps):
+        if rep == 0 or not a.cont:
+            st.reset(k, v)
         st.generate(a.n_bits, a.layout)
     st.sync()
     torch.cuda.synchronize()
