@@ -16,8 +16,7 @@
 //          taps, with the partial products b63b60, b37b33, b15b9, b60b52,
 //          b52b45, b33b28b21 and b63b45b28 shared                   23 ops
 //   output z = b1+b2+b4+b10+b31+b43+b56 + h(s3,s25,s46,s64,b63), h written
-//          as A + x2*B with A = x1+x4+x3(x0+x4), B = x3+x4(x1+x3)+x0(x1+x3+x4)
-//                                                                   11 ops
+//          as H0 + b63 H1, H0 and H1 of LFSR bits only             10 ops
 //   init   z is added into both new bits (into the LFSR's last XOR)  +1
 // Keystream words go to a ring of 160 words per thread in shared memory
 // (two bodies of 80 clocks fill five 32-clock tiles); after each body the
@@ -551,7 +550,7 @@ cudaError_t launch_grain_layout(const GrainArgs &a, const GrainQueue &q, int sm_
 
 // Logic ops per clock per 32-lane group, as written above (keystream clock
 // including z, or an initialisation clock).
-constexpr int kGrainOps = 11 + 3 + 23;
+constexpr int kGrainOps = 10 + 3 + 23;
 constexpr int kGrainInitOps = kGrainOps + 1;
 
 }  // namespace

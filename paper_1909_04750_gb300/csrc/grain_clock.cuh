@@ -26,33 +26,32 @@ __device__ __forceinline__ uint32_t xand(uint32_t a, uint32_t b, uint32_t c) {
   return lop3<0x78>(a, b, c);   // a ^ (b & c)
 }
 
-// One clock at rotation R (compile-time): returns z of the current state
-// and replaces slot R of both registers by the new bits.  The XOR sums are
-// balanced trees (at most five dependent steps to the new NFSR bit, four to
-// z), so that the instructions of one clock can issue back to back.
-template <int R, bool INIT>
-__device__ __forceinline__ uint32_t grain_clock(uint32_t (&s)[kG], uint32_t (&b)[kG]) {
-#define S(i) s[(R + (i)) % kG]
+// The filter h(x0, .., x4) = x1+x4+x0x3+x2x3+x3x4+x0x1x2+x0x2x3+x0x2x4+x1x2x4+x2x3x4
+// split by its one NFSR input x4: h = H0 + x4 H1 with H0 = x1 + x3(x0 | x2) +
+// x0x1x2 and H1 = 1 + x3 + x2(x0 + x1 + x3), both of LFSR bits only (x0..x3 =
+// s3, s25, s46, s64): 5 ops, and z = H0 + (x4 & H1) + the b sum.
+__device__ __forceinline__ void grain_h01(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                          uint32_t &h0, uint32_t &h1) {
+  h0 = xor3(x1, lop3<0xE0>(x3, x0, x2), and3(x0, x1, x2));   // 0xE0: a & (b | c)
+  h1 = lop3<0x87>(x3, x2, xor3(x0, x1, x3));                  // 0x87: ~(a ^ (b & c))
+}
+
+// z from the filter halves and the NFSR's seven linear output taps
+// b1+b2+b4+b10+b31+b43+b56 (x4 = b63): 5 ops.
+template <int R>
+__device__ __forceinline__ uint32_t grain_z(const uint32_t (&b)[kG], uint32_t h0, uint32_t h1) {
 #define B(i) b[(R + (i)) % kG]
-  // output: z = b1+b2+b4+b10+b31+b43+b56 + h(x0..x4),
-  // h = A + x2 B, A = x1+x4+x3(x0+x4), B = x3+x4(x1+x3)+x0(x1+x3+x4)
-  const uint32_t x0 = S(3), x1 = S(25), x2 = S(46), x3 = S(64), x4 = B(63);
   const uint32_t t1 = xor3(B(1), B(2), B(4));
   const uint32_t t2 = xor3(B(10), B(31), B(43));
-  const uint32_t u0 = xor3(x1, x4, B(56));
-  const uint32_t t = x0 ^ x4;
-  const uint32_t w = x1 ^ x3;
-  const uint32_t v = xor3(x1, x3, x4);
-  const uint32_t u = xor3(t1, t2, u0);                 // x1 + x4 + (b sum)
-  const uint32_t c = xand(x3, x4, w);                  // x3 + x4(x1 + x3)
-  const uint32_t a = xand(u, x3, t);                   // A + (b sum)
-  const uint32_t bb = xand(c, x0, v);                  // B
-  const uint32_t z = xand(a, x2, bb);                  // A + x2 B + (b sum)
-  // LFSR: s62+s51+s38+s23+s13+s0 (+ z while initialising)
-  const uint32_t la = xor3(S(62), S(51), S(38));
-  const uint32_t lb = xor3(S(23), S(13), S(0));
-  const uint32_t ns = INIT ? xor3(la, lb, z) : la ^ lb;
-  // NFSR: s0 + g(b), the 23 terms in a tree
+  return xor3(t1, t2, B(56)) ^ xand(h0, B(63), h1);
+#undef B
+}
+
+// NFSR feedback s0 + g(b), the 23 terms in a tree (at most five dependent
+// steps), into slot R; s0 is the LFSR's oldest bit.
+template <int R, bool INIT>
+__device__ __forceinline__ void grain_nfsr(uint32_t (&b)[kG], uint32_t s0, uint32_t z) {
+#define B(i) b[(R + (i)) % kG]
   const uint32_t p1 = B(63) & B(60);
   const uint32_t p2 = B(37) & B(33);
   const uint32_t p3 = B(15) & B(9);
@@ -63,7 +62,7 @@ __device__ __forceinline__ uint32_t grain_clock(uint32_t (&s)[kG], uint32_t (&b)
   const uint32_t l1 = xor3(B(62), B(60), B(52));
   const uint32_t l2 = xor3(B(45), B(37), B(33));
   const uint32_t l3 = xor3(B(28), B(21), B(14));
-  const uint32_t l4 = xor3(B(9), B(0), S(0));
+  const uint32_t l4 = xor3(B(9), B(0), s0);
   const uint32_t m1 = xor3(l1, l2, l3);                 // the linear terms ...
   const uint32_t m2 = xor3(l4, p1, p2);                 // ... s0, b63b60, b37b33
   const uint32_t m3 = xand(p3, q, B(45));               // b15b9, b60b52b45
@@ -77,10 +76,36 @@ __device__ __forceinline__ uint32_t grain_clock(uint32_t (&s)[kG], uint32_t (&b)
   const uint32_t n4 = xand(n2, p5, p3);                 // b33b28b21b15b9
   uint32_t nb = xor3(n1, n4, n3);
   if (INIT) nb ^= z;
-  S(0) = ns;   // slot R: the oldest bit becomes the newest
-  B(0) = nb;
-#undef S
+  B(0) = nb;   // slot R: the oldest bit becomes the newest
 #undef B
+}
+
+// LFSR feedback s62+s51+s38+s23+s13+s0 (+ z while initialising) into slot R;
+// returns the oldest bit s0 it replaces.
+template <int R, bool INIT>
+__device__ __forceinline__ uint32_t grain_lfsr(uint32_t (&s)[kG], uint32_t z) {
+#define S(i) s[(R + (i)) % kG]
+  const uint32_t s0 = S(0);
+  const uint32_t la = xor3(S(62), S(51), S(38));
+  const uint32_t lb = xor3(S(23), S(13), s0);
+  S(0) = INIT ? xor3(la, lb, z) : la ^ lb;
+  return s0;
+#undef S
+}
+
+// One clock at rotation R (compile-time): returns z of the current state
+// and replaces slot R of both registers by the new bits.  The XOR sums are
+// balanced trees, so that the instructions of one clock can issue back to
+// back: 36 ops (LFSR 3, NFSR 23, z 10), 37 while initialising.
+template <int R, bool INIT>
+__device__ __forceinline__ uint32_t grain_clock(uint32_t (&s)[kG], uint32_t (&b)[kG]) {
+#define S(i) s[(R + (i)) % kG]
+  uint32_t h0, h1;
+  grain_h01(S(3), S(25), S(46), S(64), h0, h1);
+#undef S
+  const uint32_t z = grain_z<R>(b, h0, h1);
+  const uint32_t s0 = grain_lfsr<R, INIT>(s, z);
+  grain_nfsr<R, INIT>(b, s0, z);
   return z;
 }
 

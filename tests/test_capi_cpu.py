@@ -218,9 +218,10 @@ def test_packed_offsets_match_library_sizes(L):
 
 
 def test_grain_ops_per_clock(L):
-    # output 11 (7 NFSR taps and the 5-input filter), LFSR 3 (6 taps),
-    # NFSR 23 (12 linear terms, 11 products); an init clock adds z once more
-    assert L.grain_ops_per_clock(0) == 37
-    assert L.grain_ops_per_clock(1) == 38
+    # output 10 (the 5-input filter as H0 + b63 H1 with H0, H1 of LFSR bits:
+    # 5, then b63 H1 and the 7 NFSR taps: 5), LFSR 3 (6 taps), NFSR 23 (12
+    # linear terms, 11 products); an init clock adds z once more
+    assert L.grain_ops_per_clock(0) == 36
+    assert L.grain_ops_per_clock(1) == 37
     assert not L.grain_init_streams(None, None, 4, N.MEM_HOST, None)
     assert L.mickey_last_error() == N.E_ARG

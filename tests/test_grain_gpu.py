@@ -135,6 +135,26 @@ def test_continuation_and_state():
         assert np.array_equal(got[:80], sb) and np.array_equal(got[80:], bb), i
 
 
+def test_bitsliced_calls_continue_and_export():
+    # bitsliced calls of whole 80-clock bodies and of tails continue each
+    # other exactly, and the state written back is the oracle's
+    s = workloads.grain_streams(3 * 1024 + 17, seed=21)
+    st = _gs(s)
+    ks = (160, 37, 243, 80, 1000, 1, 16, 17)
+    parts = [st.generate(k, "bitsliced").cpu().numpy().view(np.uint32) for k in ks]
+    st.sync()
+    total = sum(ks)
+    ref = og.batch_bytes(s.keys, s.ivs, total, threads=THREADS)
+    assert np.array_equal(np.concatenate(parts, axis=1), og.to_bitsliced(ref, total))
+    rec = st.export_state()
+    for i in (0, 31, 32, 1500, s.n - 1):
+        o = og.init(s.keys[i].tobytes(), s.ivs[i].tobytes())
+        og.keystream_from(o, total)
+        sb, bb = o.bits()
+        got = np.unpackbits(rec[i], bitorder="little")
+        assert np.array_equal(got[:80], sb) and np.array_equal(got[80:], bb), i
+
+
 def test_full_size_workload_sampled():
     s = workloads.grain_streams()
     n_bits = workloads.GRAIN_SCALE["n_bits"]
