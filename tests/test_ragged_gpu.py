@@ -83,6 +83,41 @@ def test_ragged_bytes_every_stream_then_continue(n):
         assert st.position(i) == int(nb[i]) + K
 
 
+@pytest.mark.parametrize("layout", ["bytes", "bitsliced"])
+def test_ragged_several_blocks_uneven_warp_groups(layout):
+    # 386 groups in several blocks, the last one partly empty; groups whose
+    # longest lanes differ widely inside a warp, every stream compared, then
+    # a plain continuation
+    n = 386 * 32 - 19
+    s = workloads.batched(n)
+    rng = np.random.default_rng(9)
+    nb = rng.integers(0, 700, n).astype(np.uint64)
+    nb[::97] = 2500
+    nb[5 * 32:6 * 32] = 0                     # a group with nothing to do
+    st = _streams(s)
+    out, offs = st.generate_ragged(nb, layout)
+    cont = st.generate(64, "bytes").cpu().numpy()
+    host = out.cpu().numpy().view(np.uint8).reshape(-1)
+    st.sync()
+    ref = _bits(s, nb + np.uint64(64))
+    if layout == "bytes":
+        for i, row in enumerate(_rows_from(out, offs, nb)):
+            assert np.array_equal(row, _pack(ref[i][: int(nb[i])])), i
+    else:
+        words_all = host.view(np.uint32)
+        for g in range((n + 31) // 32):
+            lanes = range(32 * g, min(n, 32 * g + 32))
+            C = max(int(nb[i]) for i in lanes)
+            words = words_all[int(offs[g]) // 4: int(offs[g]) // 4 + C]
+            for i in lanes:
+                got = ((words >> np.uint32(i - 32 * g)) & 1).astype(np.uint8)
+                want = np.zeros(C, np.uint8)
+                want[: int(nb[i])] = ref[i][: int(nb[i])]
+                assert np.array_equal(got, want), (g, i)
+    for i in range(n):
+        assert np.array_equal(cont[i], _pack(ref[i][int(nb[i]):])), i
+
+
 def test_ragged_bitsliced_every_stream():
     n = 70
     s = workloads.batched(n)
