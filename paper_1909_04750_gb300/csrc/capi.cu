@@ -39,6 +39,12 @@ struct mickey_streams {
   uint32_t epoch = 0;
   uint32_t spin_limit = 1u << 24;   // polls of ~256 ns before a tail piece gives up
   bool test_unpublished = false;    // test hook: tails wait for a value no head writes
+  // Keystream position of stream i = pos_base + pos[i]: a call that
+  // continues every stream by the same count moves pos_base only (O(1) host
+  // work, whatever n is); ragged calls and imports set pos[i]; pos_max is
+  // the largest pos[i], so that the 2^40 limit check of a uniform call is
+  // O(1) as well.
+  uint64_t pos_base = 0, pos_max = 0;
   std::vector<uint64_t> pos;
   // device staging for mickey_generate_host
   void *d_stage[2] = {nullptr, nullptr};
@@ -222,16 +228,20 @@ int run_init(mickey_streams *s, const void *keys, const void *ivs,
   }
   LoadArgs la{dk, di, dl, n, nullptr, s->G, s->Gpad, s->d_scratch, s->d_err};
   CUDA_TRY(launch_init(la, s->d_state, s->stream), "init_kernel launch");
-  std::fill(s->pos.begin(), s->pos.end(), 0);
+  if (s->pos_max) std::fill(s->pos.begin(), s->pos.end(), 0);
+  s->pos_base = s->pos_max = 0;
   return ok();
 }
 
 int check_limit(const mickey_streams *s, uint64_t n_bits) {
-  for (size_t i = 0; i < s->n; ++i)
-    if (s->pos[i] + n_bits > MICKEY_MAX_STREAM_BITS)
+  // positions stay at or below 2^40, so these sums cannot wrap
+  const uint64_t room = n_bits <= MICKEY_MAX_STREAM_BITS ? MICKEY_MAX_STREAM_BITS - n_bits : 0;
+  if (n_bits <= MICKEY_MAX_STREAM_BITS && s->pos_base + s->pos_max <= room) return MICKEY_OK;
+  for (size_t i = 0; i < s->n; ++i)   // name the first stream that would pass it
+    if (n_bits > MICKEY_MAX_STREAM_BITS || s->pos_base + s->pos[i] > room)
       return fail(MICKEY_E_LIMIT,
                   "stream %zu would pass 2^40 keystream bits (at %llu, +%llu)", i,
-                  (unsigned long long)s->pos[i], (unsigned long long)n_bits);
+                  (unsigned long long)(s->pos_base + s->pos[i]), (unsigned long long)n_bits);
   return MICKEY_OK;
 }
 
@@ -418,7 +428,7 @@ int mickey_generate(mickey_streams *s, uint64_t n_bits, void *out, int layout) {
                 (unsigned long long)n_bits);
   rc = launch_generate(s, n_bits, out, layout);
   if (rc) return rc;
-  for (auto &p : s->pos) p += n_bits;
+  s->pos_base += n_bits;
   return ok();
 }
 
@@ -440,7 +450,7 @@ int mickey_generate_ragged(mickey_streams *s, const uint64_t *n_bits, void *out,
     if (n_bits[i] > kMaxBitsPerCall)
       return fail(MICKEY_E_ARG, "n_bits[%zu] = %llu is above 2^34 per call", i,
                   (unsigned long long)n_bits[i]);
-    if (s->pos[i] + n_bits[i] > MICKEY_MAX_STREAM_BITS)
+    if (s->pos_base + s->pos[i] + n_bits[i] > MICKEY_MAX_STREAM_BITS)
       return fail(MICKEY_E_LIMIT, "stream %zu would pass 2^40 keystream bits", i);
     if (layout == MICKEY_LAYOUT_U32 && n_bits[i] % 32)
       return fail(MICKEY_E_LAYOUT, "the u32 layout needs n_bits[%zu] %% 32 == 0", i);
@@ -467,7 +477,7 @@ int mickey_generate_ragged(mickey_streams *s, const uint64_t *n_bits, void *out,
   if (equal_packed(n, n_bits, out_offsets, layout)) {
     const int rc = launch_generate(s, n_bits[0], out, layout);
     if (rc) return rc;
-    for (auto &p : s->pos) p += n_bits[0];
+    s->pos_base += n_bits[0];
     return ok();
   }
   // The lengths and offsets reach the kernel through one of two pinned
@@ -512,7 +522,10 @@ int mickey_generate_ragged(mickey_streams *s, const uint64_t *n_bits, void *out,
                 static_cast<uint8_t *>(out)};
   CUDA_TRY(launch_ragged(ra, layout, s->stream), "ragged_kernel launch");
   CUDA_TRY(cudaEventRecord(s->ev_ragged, s->stream), "record");
-  for (size_t i = 0; i < n; ++i) s->pos[i] += n_bits[i];
+  for (size_t i = 0; i < n; ++i) {
+    s->pos[i] += n_bits[i];
+    s->pos_max = std::max(s->pos_max, s->pos[i]);
+  }
   return ok();
 }
 
@@ -589,7 +602,7 @@ int mickey_generate_host(mickey_streams *s, uint64_t n_bits, void *host_out, int
       }
     }
     CUDA_TRY(cudaEventRecord(s->ev_copy[k], s->copy_stream), "record");
-    for (auto &p : s->pos) p += bits;
+    s->pos_base += bits;
     done += bits;
     k ^= 1;
   }
@@ -614,7 +627,7 @@ size_t mickey_num_streams(const mickey_streams *s) { return s ? s->n : 0; }
 
 uint64_t mickey_position(const mickey_streams *s, size_t i) {
   if (!s || i >= s->n) return UINT64_MAX;
-  return s->pos[i];
+  return s->pos_base + s->pos[i];
 }
 
 int mickey_export_state(mickey_streams *s, uint8_t *states, uint64_t *positions) {
@@ -632,7 +645,7 @@ int mickey_export_state(mickey_streams *s, uint8_t *states, uint64_t *positions)
         const uint32_t w = words[size_t(half * kReg + b) * s->Gpad + g];
         if ((w >> l) & 1u) rec[13 * half + b / 8] |= uint8_t(0x80u >> (b % 8));
       }
-    if (positions) positions[i] = s->pos[i];
+    if (positions) positions[i] = s->pos_base + s->pos[i];
   }
   return ok();
 }
@@ -670,6 +683,7 @@ mickey_streams *mickey_import_state(const uint8_t *states, const uint64_t *posit
         return nullptr;
       }
       s->pos[i] = positions[i];
+      s->pos_max = std::max(s->pos_max, positions[i]);
     }
   }
   cudaError_t e = cudaMemcpy(s->d_state, words.data(), words.size() * 4, cudaMemcpyHostToDevice);

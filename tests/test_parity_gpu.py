@@ -235,6 +235,52 @@ def test_limit_2_pow_40_enforced():
     assert ei.value.code == N.E_LIMIT
 
 
+def test_positions_after_uniform_and_ragged_calls():
+    # a call that continues every stream by the same count moves one common
+    # position; ragged calls and imports move single streams; the limit
+    # check and every report see their sum
+    import ctypes
+    from paper_1909_04750_gb300.streams import Streams
+    s = workloads.plain_scale(70)
+    st = _streams(s)
+    st.generate(64, "bytes")
+    lens = np.arange(70, dtype=np.uint64) * 3
+    st.generate_ragged(lens, "bytes")
+    last = st.generate(32, "bytes").cpu().numpy()
+    st.sync()
+    assert [st.position(i) for i in (0, 1, 69)] == [96, 99, 96 + 207]
+    states, pos = st.export_state()
+    assert np.array_equal(pos, 96 + lens)
+    ref = oracle.batch_bytes(s.keys, s.ivs, s.iv_lens, 96 + lens,
+                                                threads=THREADS)
+    for i in (0, 1, 33, 69):
+        bits = np.unpackbits(np.asarray(ref[i], np.uint8))[64 + int(lens[i]):96 + int(lens[i])]
+        assert np.array_equal(np.packbits(bits), last[i]), i
+    # near the 2^40 limit, with stream 5 furthest: a uniform call that only
+    # stream 5 cannot take is refused and names it; one that fits goes
+    far = np.full(70, (1 << 40) - 1000, np.uint64)
+    far[5] = (1 << 40) - 40
+    near = Streams.import_state(states, far)
+    with pytest.raises(N.MickeyError) as ei:
+        near.generate(64, "bitsliced")
+    assert ei.value.code == N.E_LIMIT and "stream 5 " in ei.value.message
+    near.generate(32, "bitsliced")
+    near.sync()
+    assert near.position(5) == (1 << 40) - 8 and near.position(0) == (1 << 40) - 968
+    L = N.lib()
+    buf = torch.empty(1 << 12, dtype=torch.uint8, device="cuda")
+    rc = L.mickey_generate(near._h, (1 << 64) - 1, ctypes.c_void_p(buf.data_ptr()),
+                           N.LAYOUT_BYTES)
+    assert rc == N.E_LIMIT and near.position(5) == (1 << 40) - 8
+    # a re-key starts every stream at 0 again
+    st.reset(torch.from_numpy(s.keys).cuda(), torch.from_numpy(s.ivs).cuda(),
+             torch.from_numpy(s.iv_lens.astype(np.int32)).cuda())
+    assert all(st.position(i) == 0 for i in (0, 5, 69))
+    again = st.generate(64, "bytes").cpu().numpy()
+    st.sync()
+    assert np.array_equal(again, _ref(s, 64))
+
+
 # -------------------------------------------------------------- full size
 
 def _sample_rows(n, k, seed):
