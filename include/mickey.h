@@ -253,7 +253,9 @@ MICKEY_API int mickey_get_config(const mickey_streams *s, int layout, int *mode,
 /* Time every configuration (mode x unroll x output tile: up to 20
  * candidates) on this handle's own streams for one call of
  * n_bits in `layout` (the state is saved and restored: positions do not
- * move), keep the fastest for that layout, and report each candidate in
+ * move), keep the fastest for that layout (among candidates within 1 % of
+ * it, the one with the deepest row staging, which moves the fewest DRAM
+ * bytes), and report each candidate in
  * results[0 .. min(max_results, *n_results)).  Synchronous; allocates a
  * temporary output buffer and a state copy.  results/n_results may be NULL. */
 MICKEY_API int mickey_tune(mickey_streams *s, uint64_t n_bits, int layout,

@@ -5,7 +5,9 @@ For a (GPU, instance count, bits per call, layout) the library's
 two-block persistent launch, 2 or 4 clocks per inner step, and the output
 tile: direct 4-byte row stores or rows staged 2, 4 or 8 tiles deep (8-, 16-
 or 32-byte row chunks) -- on the handle's own streams (state saved and
-restored) and keeps the fastest.  The
+restored) and keeps the fastest; among candidates within 1 % of it the
+deepest row staging wins (whole 32-byte sectors: the least DRAM traffic at
+the same speed).  The
 choice is cached in a JSON file next to the built library so later handles
 of the same shape reuse it without timing.
 """
@@ -70,7 +72,9 @@ def tune(streams, n_bits: int, layout: int, refresh: bool = False) -> dict:
     mode, unroll, stage = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     N.check(L.mickey_get_config(streams._h, layout, ctypes.byref(mode), ctypes.byref(unroll),
                                 ctypes.byref(stage)))
-    best = min(c["ms"] for c in cands) if cands else None
+    chosen = [c["ms"] for c in cands if (c["mode"], c["unroll"], c["stage"]) ==
+              (MODE_NAMES[mode.value], unroll.value, stage.value)]
+    best = chosen[0] if chosen else (min(c["ms"] for c in cands) if cands else None)
     entry = {"mode": mode.value, "unroll": unroll.value, "stage": stage.value, "ms": best,
              "candidates": cands}
     with _lock:
