@@ -95,6 +95,22 @@ int cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// Index of the first IV length above 80 bits in host memory, or n.  The
+// maximum of each block is taken by a loop without an early exit (so the
+// compiler vectorises it); only a block that holds an offender is scanned.
+size_t first_long_iv(const uint32_t *lens, size_t n) {
+  constexpr size_t kBlock = 4096;
+  for (size_t b = 0; b < n; b += kBlock) {
+    const size_t e = std::min(n, b + kBlock);
+    uint32_t mx = 0;
+    for (size_t i = b; i < e; ++i) mx = std::max(mx, lens[i]);
+    if (mx > MICKEY_MAX_IV_BITS)
+      for (size_t i = b; i < e; ++i)
+        if (lens[i] > MICKEY_MAX_IV_BITS) return i;
+  }
+  return n;
+}
+
 int default_mode() {
   const char *v = getenv("MICKEY_MODE");
   if (v && !strcmp(v, "grid")) return MICKEY_MODE_GRID;
@@ -201,10 +217,10 @@ int run_init(mickey_streams *s, const void *keys, const void *ivs,
   const uint8_t *dk, *di;
   const uint32_t *dl = nullptr;
   if (mem == MICKEY_MEM_HOST) {
-    if (iv_lens)
-      for (size_t i = 0; i < n; ++i)
-        if (iv_lens[i] > MICKEY_MAX_IV_BITS)
-          return fail(MICKEY_E_IVLEN, "iv_lens[%zu] = %u exceeds 80 bits", i, iv_lens[i]);
+    if (iv_lens) {
+      const size_t i = first_long_iv(iv_lens, n);
+      if (i < n) return fail(MICKEY_E_IVLEN, "iv_lens[%zu] = %u exceeds 80 bits", i, iv_lens[i]);
+    }
     // keys, IVs and lengths each at a 16-byte aligned offset (the init
     // kernel then reads them with 16-byte loads)
     const size_t rec = (n * 10 + 15) & ~size_t(15);
@@ -385,11 +401,11 @@ mickey_streams *mickey_init_streams_ex(const void *keys, const void *ivs,
     return nullptr;
   }
   if (mem == MICKEY_MEM_HOST && iv_lens) {
-    for (size_t i = 0; i < n; ++i)
-      if (iv_lens[i] > MICKEY_MAX_IV_BITS) {
-        fail(MICKEY_E_IVLEN, "iv_lens[%zu] = %u exceeds 80 bits", i, iv_lens[i]);
-        return nullptr;
-      }
+    const size_t i = first_long_iv(iv_lens, n);
+    if (i < n) {
+      fail(MICKEY_E_IVLEN, "iv_lens[%zu] = %u exceeds 80 bits", i, iv_lens[i]);
+      return nullptr;
+    }
   }
   mickey_streams *s = new (std::nothrow) mickey_streams;
   if (!s) {

@@ -76,6 +76,20 @@ def test_output_bytes(L):
     assert L.mickey_output_bytes(33, 64, 9) == 0
 
 
+def test_first_long_iv_length_is_named(L):
+    # host IV lengths are checked block by block; the error names the first
+    # length above 80, wherever it lies
+    n = 10000
+    keys = np.zeros((n, 10), np.uint8)
+    for bad in ((5000, 81), (9999, 200), (0, 81), (4095, 81), (4096, 255)):
+        lens = np.full(n, 80, np.uint32)
+        lens[bad[0]] = bad[1]
+        lens[min(n - 1, bad[0] + 3000)] = max(lens[min(n - 1, bad[0] + 3000)], 90)
+        assert not L.mickey_init_streams(keys.ctypes.data, keys.ctypes.data, lens.ctypes.data, n)
+        assert L.mickey_last_error() == N.E_IVLEN
+        assert ("iv_lens[%d] = %d" % bad).encode() in L.mickey_last_error_message(), bad
+
+
 def test_invalid_arguments_rejected_on_host(L):
     keys = np.zeros((4, 10), np.uint8)
     assert not L.mickey_init_streams(None, keys.ctypes.data, None, 4)
